@@ -7,9 +7,12 @@
  * 1606.08150): a parent thread that would launch its own child kernel for a
  * large or recursive piece of work instead appends the work to a warp-, block-
  * or grid-level buffer, and one consolidated child kernel per warp, block or
- * grid processes the whole buffer (Sec. IV.A-B). Four applications are exported
- * (Sec. V): single-source shortest paths, CSR sparse matrix-vector product, tree
- * descendants and tree heights, each at five consolidation levels.
+ * grid processes the whole buffer (Sec. IV.A-B). Seven applications of the
+ * paper's evaluation are exported (Sec. V): single-source shortest paths, CSR
+ * sparse matrix-vector product, tree descendants, tree heights, PageRank,
+ * recursive BFS and graph colouring, each at the five levels of the paper
+ * (basic-DP, flat, warp, block, grid) plus a persistent queue level; a batched
+ * engine runs many SSSP and tree problems in one resident kernel.
  *
  * Conventions shared by every entry point
  *  - All array pointers are DEVICE pointers owned by the caller. The library
@@ -66,7 +69,8 @@ typedef enum dpc_status {
   DPC_ERR_WORKSPACE = 2,   /* workspace missing or smaller than the size query returned */
   DPC_ERR_CUDA = 3,        /* a host-side CUDA call failed (launch configuration, memset, copy) */
   DPC_ERR_DEVICE = 4,      /* a device-side launch failed and the work could not be completed */
-  DPC_ERR_TIMEOUT = 5,     /* reserved: a bounded device-side wait ran out */
+  DPC_ERR_TIMEOUT = 5,     /* a bounded device-side wait (a grid barrier of the queue level or of the
+                              engine) gave up after about two seconds; see dpc_wait_selftest */
   DPC_ERR_OVERFLOW = 6,    /* a shortest-path distance reached 0xFFFFFFFF */
   DPC_ERR_UNSUPPORTED = 7, /* level or configuration not supported by this call */
   DPC_ERR_DEPTH = 8        /* recursion deeper than the device's nesting limit */
@@ -177,13 +181,22 @@ dpc_status dpc_spmv_csr(const int32_t *off, const int32_t *col, const float *val
                         void *workspace, size_t workspace_bytes, dpc_stats *stats, dpc_stream_t stream);
 
 /*
- * y = A x exactly as dpc_spmv_csr computes it, for callers that may not
+ * y = A x with the kernels and units of dpc_spmv_csr, for callers that may not
  * allocate device memory: code whose device heap belongs to another memory
  * manager (a framework's caching allocator, an inference server's arena), a
  * service with a fixed memory budget that forbids allocation after start-up,
  * or a latency-critical path on which cudaMalloc/cudaFree would synchronise
  * the device. The paper has no counterpart; this entry point is an addition of
  * the library.
+ *
+ * Levels DPC_BASIC_DP to DPC_GRID are offered; DPC_QUEUE (a cooperative
+ * launch) is not and returns DPC_ERR_INVALID_ARG. At the warp, block and grid
+ * levels, and at flat, y is bitwise the y of dpc_spmv_csr. basic-DP computes
+ * the long rows that its launch budget refuses inline, in another summation
+ * order; the budget comes from the pending-launch pool in force, which this
+ * call never sets, so call dpc_device_init first to get the pool (and the
+ * bitwise agreement) of dpc_spmv_csr; otherwise y agrees within the SpMV
+ * tolerance.
  *
  * Instead of a caller workspace it uses one scratch array of
  * DPC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
@@ -346,7 +359,11 @@ dpc_status dpc_engine_init(void *workspace, size_t workspace_bytes, int32_t slot
  * nothing is admitted. All arguments are fixed device pointers or scalars, so a
  * step can be captured in a CUDA graph and replayed after new admissions are
  * copied into the same arrays. Problems must fit the slot size (n <= max_n,
- * m <= max_m, not checked on the device). Device-side errors (a task list
+ * m <= max_m). The engine checks every admitted descriptor on the device: one
+ * that cannot be valid (unknown kind, a size beyond the slot, a missing array,
+ * a source or root out of range, a slot out of range) is not run, its slot
+ * reports 2 and the status says DPC_ERR_INVALID_ARG; the contents of the
+ * arrays (offsets, indices) are not checked. Device-side errors (a task list
  * overflow, a barrier that timed out) go to stats->status.
  */
 dpc_status dpc_engine_step(void *workspace, size_t workspace_bytes, int32_t slots, int32_t max_n, int32_t max_m,

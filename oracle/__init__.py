@@ -44,35 +44,45 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(lib):
+    """Declare the argument and result types of every oracle function on `lib`."""
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    lib.oracle_sssp_dijkstra.argtypes = [i32, P, P, P, i32, P]
+    lib.oracle_sssp_dijkstra.restype = ctypes.c_int
+    lib.oracle_sssp_frontier.argtypes = [i32, P, P, P, i32, i32, P, i64, P, P, P]
+    lib.oracle_sssp_frontier.restype = i64
+    lib.oracle_spmv_f64.argtypes = [i32, i32, P, P, P, P, P, P]
+    lib.oracle_spmv_f64.restype = ctypes.c_int
+    lib.oracle_tree_descendants.argtypes = [i32, P, P, i32, P]
+    lib.oracle_tree_descendants.restype = ctypes.c_int
+    lib.oracle_tree_height.argtypes = [i32, P, P, i32, P]
+    lib.oracle_tree_height.restype = ctypes.c_int
+    lib.oracle_tree_levels.argtypes = [i32, P, P, i32, i32, i32, P, P, P, P]
+    lib.oracle_tree_levels.restype = i32
+    lib.oracle_pagerank.argtypes = [i32, P, P, ctypes.c_double, i32, P]
+    lib.oracle_pagerank.restype = ctypes.c_int
+    lib.oracle_bfs.argtypes = [i32, P, P, i32, P]
+    lib.oracle_bfs.restype = i32
+    lib.oracle_color_jp.argtypes = [i32, P, P, P, i32, P, i64, P, P]
+    lib.oracle_color_jp.restype = i32
+    lib.oracle_consolidation_launches.argtypes = [i64, P, i32, i32, P]
+    lib.oracle_consolidation_launches.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        P = ctypes.c_void_p
-        i32, i64 = ctypes.c_int32, ctypes.c_int64
-        lib.oracle_sssp_dijkstra.argtypes = [i32, P, P, P, i32, P]
-        lib.oracle_sssp_dijkstra.restype = ctypes.c_int
-        lib.oracle_sssp_frontier.argtypes = [i32, P, P, P, i32, i32, P, i64, P, P, P]
-        lib.oracle_sssp_frontier.restype = i64
-        lib.oracle_spmv_f64.argtypes = [i32, i32, P, P, P, P, P, P]
-        lib.oracle_spmv_f64.restype = ctypes.c_int
-        lib.oracle_tree_descendants.argtypes = [i32, P, P, i32, P]
-        lib.oracle_tree_descendants.restype = ctypes.c_int
-        lib.oracle_tree_height.argtypes = [i32, P, P, i32, P]
-        lib.oracle_tree_height.restype = ctypes.c_int
-        lib.oracle_tree_levels.argtypes = [i32, P, P, i32, i32, i32, P, P, P, P]
-        lib.oracle_tree_levels.restype = i32
-        lib.oracle_pagerank.argtypes = [i32, P, P, ctypes.c_double, i32, P]
-        lib.oracle_pagerank.restype = ctypes.c_int
-        lib.oracle_bfs.argtypes = [i32, P, P, i32, P]
-        lib.oracle_bfs.restype = i32
-        lib.oracle_color_jp.argtypes = [i32, P, P, P, i32, P, i64, P, P]
-        lib.oracle_color_jp.restype = i32
-        lib.oracle_consolidation_launches.argtypes = [i64, P, i32, i32, P]
-        lib.oracle_consolidation_launches.restype = ctypes.c_int
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def load_variant(path: str):
+    """Bind a library built from another copy of dpc_oracle.c (the CPU tests
+    build deliberately broken copies to show that the pins catch them)."""
+    return _bind(ctypes.CDLL(path))
 
 
 def _c(a, dtype):

@@ -272,7 +272,6 @@ dpc_status dpc_spmv_csr(const int32_t *off, const int32_t *col, const float *val
   p.chunk = c.chunk;
   p.child_blocks = c.child_blocks;
   p.child_threads = c.child_threads;
-  p.vec = ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15u) == 0 ? 1 : 0;
   p.hdr = reinterpret_cast<WsHeader *>(workspace);
   p.stats = stats;
   p.launch_budget = launch_budget(dev);
@@ -599,7 +598,6 @@ dpc_status dpc_sssp(const int32_t *off, const int32_t *col, const uint32_t *w, i
   p.commit_blocks = c.parent_blocks;
   p.child_blocks = c.child_blocks;
   p.child_threads = c.child_threads;
-  p.vec = ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0 ? 1 : 0;
   p.heap = (c.flags & DPC_FLAG_DEVICE_MALLOC) && (level == DPC_WARP || level == DPC_BLOCK) ? 1 : 0;
   p.stream_edges = (size_t)m * (sizeof(int) + sizeof(unsigned)) > l2_bytes(dev) / 2 ? 1 : 0;
   p.launch_budget = launch_budget(dev);

@@ -63,7 +63,6 @@ struct SpmvParams {
   int max_units;
   int child_blocks;
   int child_threads;
-  int vec;  // 1 when col/val are 16-byte aligned
   float alpha;        // kModeRank: y = alpha * sum + *beta (PageRank's damping)
   const float *beta;  // kModeRank: device scalar written before the gather (teleport term)
   long long launch_budget;  // optional device launches allowed in this call
@@ -204,7 +203,6 @@ struct SsspParams {
   int commit_blocks;
   int child_blocks;
   int child_threads;
-  int vec;            // 1 when col/w are 16-byte aligned
   int max_units;
   int heap;           // 1: warp and block buffers come from the device heap (DPC_FLAG_DEVICE_MALLOC)
   int stream_edges;   // 1: col/w larger than half of L2, read with the evict-first hint

@@ -235,9 +235,4 @@ __device__ __forceinline__ int child_grid_for(int units, int kc_blocks, int chil
   return need < kc_blocks ? (need > 0 ? need : 1) : kc_blocks;
 }
 
-// Streaming loads for data read exactly once (keeps L2 for reused data).
-__device__ __forceinline__ int4 ld_stream(const int4 *p) { return __ldcs(p); }
-__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
-__device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
-
 }  // namespace dpc

@@ -75,6 +75,22 @@ int noalloc_bps(int cache[5][33], int level, const void *fn, int threads) {
   return slot;
 }
 
+// The end of a call: a launch error first, then, with DPC_FLAG_SYNC_CHECK, a
+// stream synchronisation and the device status word.
+dpc_status noalloc_finish(cudaStream_t s, unsigned flags, const WsHeader *hdr) {
+  if (cudaGetLastError() != cudaSuccess) return DPC_ERR_CUDA;
+  if (flags & DPC_FLAG_SYNC_CHECK) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return DPC_ERR_CUDA;
+    }
+    unsigned dst = 0;
+    if (cudaMemcpy(&dst, &hdr->status, sizeof(dst), cudaMemcpyDeviceToHost) != cudaSuccess) return DPC_ERR_CUDA;
+    return (dpc_status)dst;
+  }
+  return DPC_OK;
+}
+
 }  // namespace
 }  // namespace dpc
 
@@ -116,7 +132,7 @@ extern "C" dpc_status dpc_spmv_csr_noalloc(const int32_t *off, const int32_t *co
   WsHeader *hdr = reinterpret_cast<WsHeader *>(d->scratch);
   if (cudaMemsetAsync(hdr, 0, kHeaderBytes, s) != cudaSuccess) return DPC_ERR_CUDA;
   if (stats && cudaMemsetAsync(stats, 0, sizeof(dpc_stats), s) != cudaSuccess) return DPC_ERR_CUDA;
-  if (nrows == 0) return DPC_OK;
+  if (nrows == 0) return noalloc_finish(s, c.flags, hdr);
 
   if (c.parent_blocks <= 0) {
     const long long full =
@@ -147,7 +163,6 @@ extern "C" dpc_status dpc_spmv_csr_noalloc(const int32_t *off, const int32_t *co
   p.chunk = c.chunk;
   p.child_blocks = c.child_blocks;
   p.child_threads = c.child_threads;
-  p.vec = ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15u) == 0 ? 1 : 0;
   p.launch_budget = (long long)pool > reserve ? (long long)pool - reserve : 0;
   p.hdr = hdr;
   p.stats = stats;
@@ -165,14 +180,5 @@ extern "C" dpc_status dpc_spmv_csr_noalloc(const int32_t *off, const int32_t *co
     cudaGetLastError();
     return DPC_ERR_CUDA;
   }
-  if (c.flags & DPC_FLAG_SYNC_CHECK) {
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-      cudaGetLastError();
-      return DPC_ERR_CUDA;
-    }
-    unsigned dst = 0;
-    if (cudaMemcpy(&dst, &hdr->status, sizeof(dst), cudaMemcpyDeviceToHost) != cudaSuccess) return DPC_ERR_CUDA;
-    return (dpc_status)dst;
-  }
-  return DPC_OK;
+  return noalloc_finish(s, c.flags, hdr);
 }

@@ -62,6 +62,9 @@ def test_binding_constants_match_the_header():
     text = open(HEADER).read()
     flags = dict(re.findall(r"#define DPC_(FLAG_\w+)\s+(0x[0-9a-fA-F]+)u", text))
     assert flags and all(getattr(dpc, k) == int(v, 16) for k, v in flags.items())
+    # the size of the allocation-free entry point's array, (size_t)A << B in the header
+    a, b = re.search(r"#define DPC_NOALLOC_SCRATCH_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)", text).groups()
+    assert dpc.NOALLOC_SCRATCH_BYTES == int(a) << int(b)
     # struct layouts: the C compiler's sizes and offsets against the ctypes mirrors
     import shutil
     import subprocess

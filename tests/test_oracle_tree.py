@@ -50,6 +50,59 @@ def test_hand_worked():
     assert oracle.tree_height(t.coff, t.cidx, d["root"]).tolist() == d["height"]
     lv = oracle.tree_levels(t.coff, t.cidx, d["root"], threshold=2)
     assert lv.nodes.tolist() == np.bincount(d["depth"]).tolist()
+    hand = d["levels"]
+    assert lv.nodes.tolist() == hand["nodes"]
+    assert lv.internal.tolist() == hand["internal"]
+    assert lv.edges.tolist() == hand["edges"]
+    for thr, heavy in hand["heavy_by_threshold"].items():
+        assert oracle.tree_levels(t.coff, t.cidx, d["root"], threshold=int(thr)).heavy.tolist() == heavy, thr
+
+
+def levels_brute_force(parent, root, threshold):
+    """Per-depth counts from the parent array alone (no child lists): a node's
+    child count is how often it appears as a parent, its depth the length of
+    its walk to the root."""
+    n = parent.shape[0]
+    kids = np.bincount(parent[parent >= 0], minlength=n)
+    _, _, depth = brute_force(parent, root)
+    L = int(depth.max()) + 1
+    nodes = np.bincount(depth, minlength=L)
+    internal = np.bincount(depth, weights=(kids > 0), minlength=L).astype(np.int64)
+    edges = np.bincount(depth, weights=kids, minlength=L).astype(np.int64)
+    heavy = np.bincount(depth, weights=(kids > threshold), minlength=L).astype(np.int64)
+    return nodes, internal, edges, heavy
+
+
+def check_levels_against_brute_force(parent, root, thresholds=(0, 1, 2, 5, 32)):
+    t = gen.tree_from_parents(parent, root)
+    n_with_children = np.unique(parent[parent >= 0]).shape[0]
+    for thr in thresholds:
+        lv = oracle.tree_levels(t.coff, t.cidx, root, threshold=thr)
+        nodes, internal, edges, heavy = levels_brute_force(parent, root, thr)
+        assert lv.nodes.tolist() == nodes.tolist()
+        assert lv.internal.tolist() == internal.tolist()
+        assert lv.edges.tolist() == edges.tolist()
+        assert lv.heavy.tolist() == heavy.tolist()
+        # one recursive launch per node with children (Sec. IV.B): summed over depths
+        assert int(lv.internal.sum()) == n_with_children
+        assert int(lv.heavy.sum()) == int((np.bincount(parent[parent >= 0], minlength=t.n) > thr).sum())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tree_levels_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 600))
+    # random recursive trees with a few wide nodes, so that every threshold splits somewhere
+    parent = np.array([-1] + [int(rng.integers(0, max(1, i // 4))) if rng.random() < 0.5 else int(rng.integers(0, i))
+                              for i in range(1, n)], np.int64)
+    check_levels_against_brute_force(parent, 0)
+
+
+def test_tree_levels_generated_and_non_zero_root():
+    t = gen.tree(3000, heavy_p=0.02, hlo=5, hhi=60, seed=7, permute=True)
+    check_levels_against_brute_force(parents_of(t), t.root)
+    parent = np.array([2, 2, -1, 1, 1, 3, 3, 3], np.int64)  # root 2, node 3 has three children
+    check_levels_against_brute_force(parent, 2, thresholds=(0, 1, 2, 3))
 
 
 @pytest.mark.parametrize("seed", range(8))
