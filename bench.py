@@ -45,6 +45,41 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def host_cpu():
+    """The host's core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def time_oracle(fn, reps=3):
+    """Median wall time (ms) of `reps` calls of a single-threaded oracle function."""
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return float(np.median(ts))
+
+
 def job_throughput(total_ms_local, units_per_rank, steps, world, device=None):
     """Timing across ranks: the job's time is the slowest rank's (max over ranks)
     and its throughput is the units processed by all ranks over that time.
@@ -223,7 +258,7 @@ def make_flush():
 
 # ---------------------------------------------------------------- secondary measurements
 
-def bench_spmv_levels(dpc, A, x, label, steps, flush, peak, levels):
+def bench_spmv_levels(dpc, A, x, label, steps, flush, peak, levels, oracle_reps=0):
     import torch
 
     off, col, val, xd = dev(A.off), dev(A.col), dev(A.val), dev(x)
@@ -243,10 +278,22 @@ def bench_spmv_levels(dpc, A, x, label, steps, flush, peak, levels):
                       "GB/s": round(bytes_ / med / 1e6, 1), "frac_hbm": round(bytes_ / med / 1e6 / peak, 4),
                       "GFLOP/s": round(2 * A.nnz / med / 1e6, 1), "child_launches": stats.child_launches,
                       "launch_failures": stats.launch_failures, "status": stats.status}
-    return {"workload": label, "nnz": A.nnz, "algorithmic_bytes": bytes_, "levels": res}
+    out = {"workload": label, "nnz": A.nnz, "algorithmic_bytes": bytes_, "levels": res}
+    if oracle_reps > 0:
+        import oracle  # the CPU baseline: the oracle as it stands, one thread
+
+        ms_o = time_oracle(lambda: oracle.spmv_f64(A.off, A.col, A.val, x), oracle_reps)
+        out["oracle"] = {"kind": "oracle", "what": "fp64 row sums, one thread", "cores": 1, "reps": oracle_reps,
+                         "ms": round(ms_o, 2), "GB/s": round(bytes_ / ms_o / 1e6, 3), "host": host_cpu()}
+        for level in levels:
+            res[level]["speedup_vs_oracle"] = round(ms_o / res[level]["ms"], 2)
+    return out
 
 
-def bench_sssp(dpc, g, sources, label, steps, flush, levels):
+def bench_sssp(dpc, g, sources, label, steps, flush, levels, oracle_reps=0, tuning=None):
+    """Every level on every source: per source the median of `steps` calls
+    (after one untimed call), then the mean over sources. With oracle_reps > 0
+    the CPU oracle (Dijkstra, one thread) is timed on every source too."""
     import torch
 
     off, col, w = dev(g.off), dev(g.col), dev(g.w)
@@ -256,30 +303,49 @@ def bench_sssp(dpc, g, sources, label, steps, flush, levels):
     deg = np.diff(g.off).astype(np.int64)
     teps_edges = {}
     for level in levels:
-        ws = torch.empty(dpc.sssp_workspace_size(g.n, g.m, level), dtype=torch.uint8, device="cuda")
+        ws = torch.empty(dpc.sssp_workspace_size(g.n, g.m, level, tuning), dtype=torch.uint8, device="cuda")
         st = dpc.new_stats()
         per_src = []
         for src in sources:
-            fn = lambda: dpc.sssp(off, col, w, src, dist, level, workspace=ws, stats=st)
+            fn = lambda: dpc.sssp(off, col, w, src, dist, level, tuning=tuning, workspace=ws, stats=st)
             t = time_calls(fn, steps, 1, s, flush)
             if src not in teps_edges:
                 # Graph500 convention: edges whose source vertex is reachable from the root
                 reached = dist.cpu().numpy().view(np.uint32) != 0xFFFFFFFF
                 teps_edges[src] = int(deg[reached].sum())
-            per_src.append((float(np.median(t)), teps_edges[src], dpc.read_stats(st)))
+            per_src.append((float(np.median(t)), teps_edges[src], dpc.read_stats(st), src))
         ms = float(np.mean([p[0] for p in per_src]))
         gteps = float(np.mean([p[1] / p[0] / 1e6 for p in per_src]))
         last = per_src[-1][2]
         res[level] = {"ms": round(ms, 4), "GTEPS": round(gteps, 4), "rounds": last.rounds,
                       "relaxations": last.relaxations, "child_launches": last.child_launches,
                       "aux_launches": last.aux_launches, "launch_failures": last.launch_failures,
-                      "status": last.status}
+                      "status": max(p[2].status for p in per_src), "steps_per_source": steps}
+        if len(sources) > 1:
+            res[level]["per_source"] = [
+                {"source": p[3], "ms": round(p[0], 4), "GTEPS": round(p[1] / p[0] / 1e6, 3), "rounds": p[2].rounds,
+                 "relaxations": p[2].relaxations, "launch_failures": p[2].launch_failures,
+                 "reachable_edges": p[1]} for p in per_src]
+            res[level]["launch_failures"] = sum(p[2].launch_failures for p in per_src)
     for level in levels:
         if "flat" in res:
             res[level]["speedup_vs_flat"] = round(res["flat"]["ms"] / res[level]["ms"], 3)
         if "basic_dp" in res:
             res[level]["speedup_vs_basic_dp"] = round(res["basic_dp"]["ms"] / res[level]["ms"], 3)
-    return {"workload": label, "n": g.n, "m": g.m, "sources": sources, "levels": res}
+    out = {"workload": label, "n": g.n, "m": g.m, "sources": sources, "levels": res}
+    if oracle_reps > 0:
+        import oracle  # the CPU baseline: the oracle as it stands, one thread
+
+        per = [time_oracle(lambda: oracle.sssp_dijkstra(g.off, g.col, g.w, src), oracle_reps) for src in sources]
+        ms_o = float(np.mean(per))
+        out["oracle"] = {"kind": "oracle", "what": "binary-heap Dijkstra (fp64-free, uint64 sums), one thread",
+                         "cores": 1, "ms": round(ms_o, 2), "reps_per_source": oracle_reps,
+                         "GTEPS": round(float(np.mean([teps_edges[sv] / t / 1e6 for sv, t in zip(sources, per)])),
+                                        5),
+                         "per_source_ms": [round(t, 2) for t in per], "host": host_cpu()}
+        for level in levels:
+            res[level]["speedup_vs_oracle"] = round(ms_o / res[level]["ms"], 2)
+    return out
 
 
 def pagerank_bytes(n, m, iters):
@@ -289,7 +355,7 @@ def pagerank_bytes(n, m, iters):
     return iters * (4 * m + 24 * n + 4)
 
 
-def bench_pagerank(dpc, g, label, steps, levels, iters=20, damping=0.85):
+def bench_pagerank(dpc, g, label, steps, levels, iters=20, damping=0.85, oracle_reps=0):
     import torch
 
     ie = gen_in_edges(g)
@@ -316,8 +382,17 @@ def bench_pagerank(dpc, g, label, steps, levels, iters=20, damping=0.85):
             res[level]["speedup_vs_flat"] = round(res["flat"]["ms"] / res[level]["ms"], 3)
         if "basic_dp" in res:
             res[level]["speedup_vs_basic_dp"] = round(res["basic_dp"]["ms"] / res[level]["ms"], 3)
-    return {"workload": label, "n": ie.n, "m": ie.m, "iterations": iters, "damping": damping,
-            "algorithmic_bytes": bytes_, "levels": res}
+    out = {"workload": label, "n": ie.n, "m": ie.m, "iterations": iters, "damping": damping,
+           "algorithmic_bytes": bytes_, "levels": res}
+    if oracle_reps > 0:
+        import oracle  # the CPU baseline: the oracle as it stands, one thread
+
+        ms_o = time_oracle(lambda: oracle.pagerank(g.off, g.col, damping, iters), oracle_reps)
+        out["oracle"] = {"kind": "oracle", "what": "fp64 power iteration pushed along out-edges, one thread",
+                         "cores": 1, "reps": oracle_reps, "ms": round(ms_o, 2), "host": host_cpu()}
+        for level in levels:
+            res[level]["speedup_vs_oracle"] = round(ms_o / res[level]["ms"], 2)
+    return out
 
 
 def gen_in_edges(g):
@@ -326,7 +401,7 @@ def gen_in_edges(g):
     return gen.in_edges(g.off, g.col)
 
 
-def bench_bfs(dpc, g, sources, label, steps, levels):
+def bench_bfs(dpc, g, sources, label, steps, levels, oracle_reps=0):
     """Recursive BFS; GTEPS counts the out-edges of the vertices reached from
     the source (Graph500 convention)."""
     import torch
@@ -358,7 +433,16 @@ def bench_bfs(dpc, g, sources, label, steps, levels):
             res[level]["speedup_vs_flat"] = round(res["flat"]["ms"] / res[level]["ms"], 3)
         if "basic_dp" in res:
             res[level]["speedup_vs_basic_dp"] = round(res["basic_dp"]["ms"] / res[level]["ms"], 3)
-    return {"workload": label, "n": g.n, "m": g.m, "sources": sources, "levels": res}
+    out = {"workload": label, "n": g.n, "m": g.m, "sources": sources, "levels": res}
+    if oracle_reps > 0:
+        import oracle  # the CPU baseline: the oracle as it stands, one thread
+
+        ms_o = float(np.mean([time_oracle(lambda: oracle.bfs(g.off, g.col, src), oracle_reps) for src in sources]))
+        out["oracle"] = {"kind": "oracle", "what": "FIFO-queue BFS, one thread", "cores": 1, "reps": oracle_reps,
+                         "ms": round(ms_o, 2), "host": host_cpu()}
+        for level in levels:
+            res[level]["speedup_vs_oracle"] = round(ms_o / res[level]["ms"], 2)
+    return out
 
 
 def bench_gc(dpc, off, col, prio, label, steps, levels):
@@ -388,7 +472,7 @@ def bench_gc(dpc, off, col, prio, label, steps, levels):
     return {"workload": label, "n": n, "m": m, "levels": res}
 
 
-def bench_tree(dpc, t, label, steps, levels):
+def bench_tree(dpc, t, label, steps, levels, oracle_reps=0):
     import torch
 
     coff, cidx = dev(t.coff), dev(t.cidx)
@@ -414,7 +498,19 @@ def bench_tree(dpc, t, label, steps, levels):
                 res[level][op]["speedup_vs_flat"] = round(res["flat"][op]["ms"] / res[level][op]["ms"], 3)
             if "basic_dp" in res:
                 res[level][op]["speedup_vs_basic_dp"] = round(res["basic_dp"][op]["ms"] / res[level][op]["ms"], 3)
-    return {"workload": label, "n": t.n, "levels": res}
+    out = {"workload": label, "n": t.n, "levels": res}
+    if oracle_reps > 0:
+        import oracle  # the CPU baseline: the oracle as it stands, one thread
+
+        ms_d = time_oracle(lambda: oracle.tree_descendants(t.coff, t.cidx, 0), oracle_reps)
+        ms_h = time_oracle(lambda: oracle.tree_height(t.coff, t.cidx, 0), oracle_reps)
+        out["oracle"] = {"kind": "oracle", "what": "post-order DFS with an explicit stack, one thread", "cores": 1,
+                         "reps": oracle_reps, "descendants_ms": round(ms_d, 2), "height_ms": round(ms_h, 2),
+                         "descendants_Mnodes/s": round(t.n / ms_d / 1e3, 2), "host": host_cpu()}
+        for level in levels:
+            res[level]["descendants"]["speedup_vs_oracle"] = round(ms_d / res[level]["descendants"]["ms"], 2)
+            res[level]["height"]["speedup_vs_oracle"] = round(ms_h / res[level]["height"]["ms"], 2)
+    return out
 
 
 def bench_alloc_study(dpc):
@@ -602,7 +698,8 @@ def run_reference(args, rank, world):
         "config": {"workload": headline_workload(args.level, A.nrows, 1.5), "nnz": A.nnz, "level": args.level,
                    "implementation": "CPU oracle, fp64, 1 thread (bounded row-block samples)",
                    "parallelism": "replicas x1"},
-        "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample_desc},
+        "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample_desc,
+                         "host": host_cpu()},
         "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -629,27 +726,32 @@ def run_apps(dpc, levels, steps, peak, A=None, x=None):
     del A
     torch.cuda.empty_cache()
     A2 = gen.zipf_csr(N_SPMV, N_SPMV, s=1.8795, lmax=200_000, seed=3)
+    with_oracle = any(lv != "basic_dp" for lv in levels)  # the oracle is timed once, in the main process
     apps["spmv_zipf_mean16"] = bench_spmv_levels(dpc, A2, x, "1Mx1M zipf s=1.8795 (mean 16, nnz ~1.7e7)",
-                                                 max(5, steps), flush, peak, levels)
+                                                 max(5, steps), flush, peak, levels,
+                                                 oracle_reps=3 if with_oracle else 0)
     del A2
     g12 = gen.rmat(12, seed=1)
-    apps["sssp_rmat12"] = bench_sssp(dpc, g12, [0], "R-MAT scale 12, w in [1,100], source 0", 10, None, levels)
-    if any(lv != "basic_dp" for lv in levels):  # basic-DP is not timed at this size
-        g22 = gen.rmat(22, whi=1000, seed=2)
-        rng = np.random.default_rng(2)
-        srcs = [int(s_) for s_ in rng.choice(np.nonzero(np.diff(g22.off) > 0)[0], 8, replace=False)]
-        apps["sssp_rmat22"] = bench_sssp(dpc, g22, srcs[:2], "R-MAT scale 22, w in [1,1000], 2 of 8 sources", 2,
-                                         flush, [lv for lv in levels if lv != "basic_dp"])
-        del g22
+    apps["sssp_rmat12"] = bench_sssp(dpc, g12, [0], "R-MAT scale 12, w in [1,100], source 0", 10, None, levels,
+                                     oracle_reps=3 if with_oracle else 0)
+    g22 = gen.rmat(22, whi=1000, seed=2)
+    rng = np.random.default_rng(2)
+    srcs = [int(s_) for s_ in rng.choice(np.nonzero(np.diff(g22.off) > 0)[0], 8, replace=False)]
+    # every level on all 8 sources, 5 timed calls each with L2 flushed before each; basic-DP
+    # runs with the large launch pool of its own process (refused launches are relaxed inline)
+    apps["sssp_rmat22"] = bench_sssp(dpc, g22, srcs, "R-MAT scale 22, w in [1,1000], 8 random sources", 5,
+                                     flush, levels, oracle_reps=1 if with_oracle else 0)
+    del g22
     g19 = gen.rmat(19, edge_factor=32, seed=6)
     apps["pagerank_rmat19"] = bench_pagerank(
         dpc, g19, "PageRank, R-MAT scale 19 edge factor 32 (524,288 vertices, 16.8M edges), 20 iterations, d=0.85",
-        5, levels)
+        5, levels, oracle_reps=1 if with_oracle else 0)
     del g19
     g16 = gen.rmat(16, edge_factor=80, seed=7)
     apps["bfs_rec_kron16"] = bench_bfs(
         dpc, g16, [0, int(np.random.default_rng(7).integers(1, g16.n))],
-        "recursive BFS, R-MAT scale 16 edge factor 80 (65,536 vertices, 5.2M edges; Kron_log16's shape)", 5, levels)
+        "recursive BFS, R-MAT scale 16 edge factor 80 (65,536 vertices, 5.2M edges; Kron_log16's shape)", 5, levels,
+        oracle_reps=3 if with_oracle else 0)
     del g16
     g16 = gen.rmat(16, edge_factor=40, seed=7)
     s_off, s_col = gen.symmetrize(g16.off, g16.col)
@@ -659,7 +761,8 @@ def run_apps(dpc, levels, steps, peak, A=None, x=None):
         "edges; Kron_log16's shape)", 5, levels)
     del g16, s_off, s_col
     t4 = gen.tree(2_097_152, seed=4)
-    apps["tree_2m"] = bench_tree(dpc, t4, "2,097,152-node heavy-tailed tree", 5, levels)
+    apps["tree_2m"] = bench_tree(dpc, t4, "2,097,152-node heavy-tailed tree", 5, levels,
+                                 oracle_reps=3 if with_oracle else 0)
     del t4
     # the paper's depth-5 tree datasets (Sec. V): not for basic-DP, whose one
     # recursive launch per internal node (up to 0.9 M) is beyond the launch pool
@@ -719,6 +822,11 @@ def merge_levels(apps, extra):
                     if "basic_dp" in lv:
                         b = lv["basic_dp"] if op is None else lv["basic_dp"][op]
                         r["speedup_vs_basic_dp"] = round(b["ms"] / r["ms"], 3)
+                    o = res.get("oracle")
+                    if o is not None:  # the oracle timed in the main process
+                        o_ms = o.get("ms") if op is None else o.get(f"{op}_ms")
+                        if o_ms:
+                            r["speedup_vs_oracle"] = round(o_ms / r["ms"], 2)
 
 
 # ---------------------------------------------------------------- per-level ncu ranges
@@ -973,7 +1081,8 @@ def main():
             passes += 1
         sec = (time.perf_counter() - t0) / passes
         cpu = {"value": round(bytes_ / sec / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"{passes} full passes of the headline matrix (fp64, single thread), {sec:.2f} s each"}
+               "sample": f"{passes} full passes of the headline matrix (fp64, single thread), {sec:.2f} s each",
+               "host": host_cpu()}
 
     apps = {}
     if not args.no_apps and rank == 0:

@@ -17,6 +17,10 @@
  *                             with per-round frontier sizes and the number of
  *                             frontier vertices above THRESHOLD (the per-thread
  *                             child launches of basic-DP)
+ *   oracle_sssp_nearfar       the frontier rounds with a near-far split of the
+ *                             vertices that dropped (near: relaxed next round;
+ *                             far: kept until the split distance passes them),
+ *                             after Davidson et al., IPDPS 2014
  *   oracle_spmv_f64           y = A x for CSR A in double precision (Sec. V,
  *                             SpMV benchmark; irregular loop of Sec. II.B)
  *   oracle_tree_descendants   number of proper descendants of every node
@@ -188,6 +192,115 @@ int64_t oracle_sssp_frontier(int32_t n, const int32_t *off, const int32_t *col, 
   }
   *relaxations = relax;
   free(d); free(dprev); free(F); free(G); free(in_next);
+  return bad ? -1 : rounds;
+}
+
+/*
+ * Near-far frontier rounds: the rounds of oracle_sssp_frontier with the
+ * near-far work split of Davidson, Baxter, Garland & Owens ("Work-Efficient
+ * Parallel GPU Methods for Single-Source Shortest Paths", IPDPS 2014) put in
+ * front of them. A split distance S, always a multiple of delta, divides the
+ * vertices whose distance dropped in a round: those with d < S form the next
+ * frontier (the near set), the others join the far pile (a set: a vertex is in
+ * it at most once). A round is the Jacobi round of oracle_sssp_frontier on the
+ * near set. When a round leaves the near set empty the split advances:
+ *   - far-pile vertices with d < S were relaxed with their current distance
+ *     already (they dropped below S, so they went through the near set) and
+ *     are dropped;
+ *   - dmin = the smallest distance among the others; S becomes
+ *     delta * (floor(dmin / delta) + 1), the top of dmin's bucket;
+ *   - far-pile vertices with d < S (the new) leave the pile and form the near set.
+ * The run ends when the near set and the far pile are both empty. delta = 0
+ * means no split (S infinite): exactly the rounds of oracle_sssp_frontier.
+ *
+ * Per round r: frontier_size[r] = near-set size, heavy[r] = its vertices with
+ * out-degree above threshold. *relaxations = edges examined, *splits = split
+ * advances. Returns the number of rounds, or -1 on bad arguments / more than
+ * max_rounds rounds / distance overflow.
+ */
+int64_t oracle_sssp_nearfar(int32_t n, const int32_t *off, const int32_t *col, const uint32_t *w, int32_t source,
+                            uint32_t delta, int32_t threshold, uint32_t *dist_out, int64_t max_rounds,
+                            int64_t *frontier_size, int64_t *heavy, int64_t *relaxations, int64_t *splits) {
+  if (n < 1 || source < 0 || source >= n) return -1;
+  uint64_t *d = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  uint64_t *dprev = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  int32_t *near = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *changed = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *far = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  uint8_t *in_changed = (uint8_t *)calloc((size_t)n, 1);
+  uint8_t *in_far = (uint8_t *)calloc((size_t)n, 1);
+  if (!d || !dprev || !near || !changed || !far || !in_changed || !in_far) {
+    free(d); free(dprev); free(near); free(changed); free(far); free(in_changed); free(in_far);
+    return -1;
+  }
+  for (int32_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
+  d[source] = 0;
+  uint64_t S = delta ? (uint64_t)delta : UINT64_MAX;
+  int64_t nnear = 1, nfar = 0, rounds = 0, relax = 0, nsplit = 0;
+  near[0] = source;
+  int bad = 0;
+  for (;;) {
+    if (nnear == 0) {
+      if (nfar == 0) break;
+      /* advance the split */
+      uint64_t dmin = UINT64_MAX;
+      for (int64_t i = 0; i < nfar; ++i)
+        if (d[far[i]] >= S && d[far[i]] < dmin) dmin = d[far[i]];
+      if (dmin == UINT64_MAX) { /* every far vertex was stale */
+        for (int64_t i = 0; i < nfar; ++i) in_far[far[i]] = 0;
+        nfar = 0;
+        break;
+      }
+      const uint64_t S_old = S;
+      S = (dmin / delta + 1) * (uint64_t)delta;
+      nsplit++;
+      int64_t keep = 0;
+      for (int64_t i = 0; i < nfar; ++i) {
+        int32_t v = far[i];
+        if (d[v] < S_old) { in_far[v] = 0; continue; }             /* relaxed already */
+        if (d[v] < S) { in_far[v] = 0; near[nnear++] = v; continue; } /* the new near set */
+        far[keep++] = v;
+      }
+      nfar = keep;
+      continue;
+    }
+    if (rounds >= max_rounds) { bad = 1; break; }
+    int64_t hv = 0;
+    for (int64_t i = 0; i < nnear; ++i) if (off[near[i] + 1] - off[near[i]] > threshold) hv++;
+    frontier_size[rounds] = nnear;
+    heavy[rounds] = hv;
+    for (int64_t i = 0; i < nnear; ++i) dprev[near[i]] = d[near[i]];
+    int64_t nc = 0;
+    for (int64_t i = 0; i < nnear; ++i) {
+      int32_t u = near[i];
+      for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+        int32_t v = col[e];
+        uint64_t nd = dprev[u] + (uint64_t)w[e];
+        relax++;
+        if (nd < d[v]) {
+          d[v] = nd;
+          if (!in_changed[v]) { in_changed[v] = 1; changed[nc++] = v; }
+        }
+      }
+    }
+    rounds++;
+    /* split the vertices that dropped into the next near set and the far pile */
+    nnear = 0;
+    for (int64_t i = 0; i < nc; ++i) {
+      int32_t v = changed[i];
+      in_changed[v] = 0;
+      if (d[v] < S) near[nnear++] = v;
+      else if (!in_far[v]) { in_far[v] = 1; far[nfar++] = v; }
+    }
+  }
+  for (int32_t v = 0; v < n; ++v) {
+    if (d[v] == UINT64_MAX) dist_out[v] = ORACLE_INF;
+    else if (d[v] >= ORACLE_INF) { dist_out[v] = ORACLE_INF; bad = 1; }
+    else dist_out[v] = (uint32_t)d[v];
+  }
+  *relaxations = relax;
+  if (splits) *splits = nsplit;
+  free(d); free(dprev); free(near); free(changed); free(far); free(in_changed); free(in_far);
   return bad ? -1 : rounds;
 }
 

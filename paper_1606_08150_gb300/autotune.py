@@ -69,20 +69,44 @@ def search(run: Callable[[dpc.Tuning], None], space: Iterable[Dict[str, int]], r
     return best.params, trials
 
 
+# child_blocks that no buffer reaches: the child grid is then sized by the
+# buffer alone, one warp per buffered unit (the paper's "1-1 mapping", Sec. V.B)
+ONE_TO_ONE_BLOCKS = 1 << 30
+DEFAULT_CHILD_THREADS = 256
+
+
 def kc_study(run_level: Callable[[str, dpc.Tuning], None], levels: Sequence[str] = ("grid", "block", "warp"),
              kcs: Sequence[int] = (1, 2, 4, 8, 16, 32, 64), child_threads: Sequence[int] = (128, 256, 512),
-             reps: int = 5) -> Dict[str, Dict[str, float]]:
-    """For every level: time of the KC_X rule's configuration, the best one found
-    by exhaustive search over (X, child threads), and their ratio (Fig. 6's
-    comparison, in kind)."""
+             reps: int = 5, passes: int = 2) -> Dict[str, Dict[str, float]]:
+    """Fig. 6's comparison, in kind, for every level: the KC_X rule's
+    configuration (X of the level, default child blocks of 256 threads), the
+    1-1 mapping (as many child warps as buffered units, whatever the
+    occupancy) and the best configuration of an exhaustive search over (X,
+    child threads). All candidates are timed in the same sweep, `passes` times
+    in interleaved order, keeping each one's fastest median; the rule is one of
+    the searched candidates, so the search never reports worse than the rule."""
     out = {}
     for level in levels:
-        rule = dpc.Tuning(kc=KC_RULE[level])
-        t_rule = time_call(lambda: run_level(level, rule), reps)
-        best_p, trials = search(lambda t: run_level(level, t), grid_space(kc=kcs, child_threads=child_threads), reps)
-        t_best = min(tr.ms for tr in trials)
+        rule = {"kc": KC_RULE[level], "child_threads": DEFAULT_CHILD_THREADS}
+        space = grid_space(kc=kcs, child_threads=child_threads)
+        if rule not in space:
+            space.append(rule)
+        one = {"child_blocks": ONE_TO_ONE_BLOCKS, "child_threads": DEFAULT_CHILD_THREADS}
+        cands = space + [one]
+        best_ms = [float("inf")] * len(cands)
+        for k in range(passes):
+            order = range(len(cands)) if k % 2 == 0 else reversed(range(len(cands)))
+            for i in order:
+                t = dpc.Tuning(**cands[i])
+                best_ms[i] = min(best_ms[i], time_call(lambda: run_level(level, t), reps))
+        searched = best_ms[:len(space)]
+        ib = int(np.argmin(searched))
+        t_rule = searched[space.index(rule)]
+        t_best = searched[ib]
+        t_one = best_ms[-1]
         out[level] = {"rule_kc": KC_RULE[level], "rule_ms": round(t_rule, 4), "best_ms": round(t_best, 4),
-                      "best": best_p, "rule_fraction_of_best": round(t_best / t_rule, 4)}
+                      "best": space[ib], "rule_fraction_of_best": round(t_best / t_rule, 4),
+                      "one_to_one_ms": round(t_one, 4), "one_to_one_fraction_of_best": round(t_best / t_one, 4)}
     return out
 
 

@@ -176,3 +176,37 @@ def test_graph_capture_and_replay(dpc):
         g.replay()
         torch.cuda.synchronize()
         check(probs, outs)
+
+
+def test_upper_sizes_of_the_served_mix(dpc):
+    """The largest problems of the served stream (an R-MAT 2^18 graph, edge
+    factor 16, weights in [1,100]; a 10^6-node heavy-tailed tree for
+    descendants and for heights) inside a mixed batch with small problems:
+    bit-exact against the oracle, and the same alone as in the mix."""
+    g = gen.rmat(18, seed=1018)
+    src = int(np.nonzero(np.diff(g.off) > 0)[0][3])
+    t = gen.tree(1_000_000, seed=2018)
+    big = [("sssp", g, src, oracle.sssp_dijkstra(g.off, g.col, g.w, src)),
+           ("desc", t, 0, oracle.tree_descendants(t.coff, t.cidx, 0)),
+           ("height", t, 0, oracle.tree_height(t.coff, t.cidx, 0))]
+    probs = big + make_problems(3, 9)
+    jobs, keep, outs = to_jobs(dpc, probs)
+    max_n = max(p[1].n for p in probs)
+    max_m = max(p[1].m if p[0] == "sssp" else p[1].n for p in probs)
+    e = Eng(dpc, len(jobs), max_n, max_m)
+    e.stage(jobs, list(range(len(jobs))))
+    e.step(1 << 30)
+    torch.cuda.synchronize()
+    assert dpc.read_stats(e.stats).status == 0
+    assert (e.state.cpu().numpy() == 2).all()
+    check(probs, outs)
+    mixed = [o.clone() for o in outs[:len(big)]]
+    e1 = Eng(dpc, 1, max_n, max_m)
+    for i in range(len(big)):
+        outs[i].fill_(-5)
+        dpc.engine_init(e1.ws, 1, max_n, max_m, e1.state, None)
+        e1.stage([jobs[i]], [0])
+        e1.step(1 << 30)
+        torch.cuda.synchronize()
+        assert dpc.read_stats(e1.stats).status == 0
+        assert torch.equal(outs[i], mixed[i]), probs[i][0]

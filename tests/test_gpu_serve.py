@@ -69,6 +69,54 @@ def test_mixed_stream_matches_alone_and_oracle(dpc, pool, rate, slots, waves, us
         assert np.array_equal(alone[i], got[i]), i
 
 
+@pytest.fixture(scope="module")
+def pool_upper():
+    """The served stream's size range up to its top (R-MAT 2^18, trees of 10^6 nodes)."""
+    graphs, graphs_h, sources = [], [], []
+    for i, scale in enumerate([10, 14, 18]):
+        g = gen.rmat(scale, seed=300 + i)
+        graphs_h.append(g)
+        graphs.append(serve.upload_graph(g))
+        sources.append(np.nonzero(np.diff(g.off) > 0)[0])
+    trees, trees_h = [], []
+    for i, n in enumerate([1000, 100_000, 1_000_000]):
+        t = gen.tree(n, seed=400 + i, permute=bool(i % 2))
+        trees_h.append(t)
+        trees.append(serve.upload_tree(t))
+    return graphs, graphs_h, sources, trees, trees_h
+
+
+def test_upper_sizes_in_the_stream_match_alone_and_oracle(dpc, pool_upper):
+    graphs, graphs_h, sources, trees, trees_h = pool_upper
+    rng = np.random.default_rng(19)
+    reqs = serve.poisson_stream(rng, 48, 5000.0, len(graphs), len(trees), sources)
+    # every request on the largest graph and the largest tree is in the stream at least once
+    reqs += [serve.Request(dpc.JOB_SSSP, 2, int(sources[2][7]), reqs[-1].arrival),
+             serve.Request(dpc.JOB_TREE_DESCENDANTS, 2, 0, reqs[-1].arrival),
+             serve.Request(dpc.JOB_TREE_HEIGHT, 2, 0, reqs[-1].arrival)]
+    srv = serve.Server(graphs, trees, slots=8, waves_per_step=16)
+    got = {}
+
+    def keep(i, s):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        got[i] = srv.out[s, :n].cpu().numpy().copy()
+
+    res = srv.run(reqs, on_done=keep)
+    assert res.status == 0 and len(got) == len(reqs)
+    alone = {}
+
+    def keep_alone(i, out):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        alone[i] = out[:n].cpu().numpy().copy()
+
+    serve.one_at_a_time(graphs, trees, [serve.Request(r.kind, r.problem, r.source, 0.0) for r in reqs],
+                        on_done=keep_alone)
+    for i, r in enumerate(reqs):
+        want = expected(r, graphs_h, trees_h)
+        assert np.array_equal(got[i], want), i
+        assert np.array_equal(alone[i], got[i]), i
+
+
 def test_slots_follow_free_memory(dpc):
     small = serve.slots_for_memory(1000, 16000, 64 << 20)
     big = serve.slots_for_memory(1000, 16000, 512 << 20)

@@ -64,6 +64,80 @@ def test_hand_worked_instance():
     assert fr.relaxations == d["relaxations"]
 
 
+def test_hand_worked_near_far():
+    d = json.load(open(os.path.join(GOLDEN, "sssp_hand.json")))
+    off, col, w = csr_from_edges(d["n"], d["edges"])
+    for delta, want in d["nearfar"].items():
+        r = oracle.sssp_nearfar(off, col, w, d["source"], int(delta), d["threshold"])
+        np.testing.assert_array_equal(r.dist, np.array(d["dist"], np.uint32))
+        assert r.frontier_size.tolist() == want["frontier_size"], delta
+        assert r.heavy.tolist() == want["heavy"], delta
+        assert (r.relaxations, r.splits) == (want["relaxations"], want["splits"]), delta
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_near_far_matches_floyd_warshall(seed):
+    rng = np.random.default_rng(50 + seed)
+    n = int(rng.integers(1, 65))
+    g = gen.random_graph(n, int(rng.integers(0, 4 * n + 1)), 0 if seed % 3 == 0 else 1, int(rng.integers(1, 300)),
+                         seed=seed)
+    fw = floyd_warshall(n, g.off, g.col, g.w)
+    for s in range(0, n, 3):
+        for delta in (1, 7, 50, 1 << 30):
+            np.testing.assert_array_equal(oracle.sssp_nearfar(g.off, g.col, g.w, s, delta, 2).dist, as_u32(fw[s]))
+
+
+@pytest.mark.parametrize("scale,seed", [(8, 1), (10, 2), (12, 1)])
+def test_near_far_width_one_relaxes_each_vertex_once(scale, seed):
+    """Width 1 with weights >= 1: a bucket holds one distance value, whose
+    vertices are final when it is relaxed (Dijkstra's argument), so each
+    reached vertex is relaxed exactly once and the rounds are the distinct
+    distances in increasing order."""
+    g = gen.rmat(scale, seed=seed)
+    assert g.w.min() >= 1
+    d = oracle.sssp_dijkstra(g.off, g.col, g.w, 0)
+    deg = np.diff(g.off)
+    reached = d != INF
+    values, counts = np.unique(d[reached], return_counts=True)
+    thr = 20
+    heavy = [int(((d == v) & (deg > thr)).sum()) for v in values]
+    r = oracle.sssp_nearfar(g.off, g.col, g.w, 0, 1, thr)
+    np.testing.assert_array_equal(r.dist, d)
+    assert r.frontier_size.tolist() == counts.tolist()
+    assert r.heavy.tolist() == heavy
+    assert r.relaxations == int(deg[reached].sum())
+    assert r.splits == r.rounds - 1
+
+
+@pytest.mark.parametrize("scale,seed", [(9, 3), (12, 1)])
+def test_near_far_without_a_split_is_the_plain_rounds(scale, seed):
+    """delta = 0 (no split) and a width above every distance both leave the far
+    pile empty: the frontier rounds exactly."""
+    g = gen.rmat(scale, whi=1000, seed=seed)
+    fr = oracle.sssp_frontier(g.off, g.col, g.w, 0, 32)
+    for delta in (0, 1 << 31):
+        r = oracle.sssp_nearfar(g.off, g.col, g.w, 0, delta, 32)
+        np.testing.assert_array_equal(r.dist, fr.dist)
+        assert r.frontier_size.tolist() == fr.frontier_size.tolist()
+        assert r.heavy.tolist() == fr.heavy.tolist()
+        assert (r.relaxations, r.splits) == (fr.relaxations, 0)
+
+
+def test_near_far_path_closed_form():
+    # path with weight i+1 on edge i: d(j) = j(j+1)/2, one vertex per round whatever the width
+    k = 40
+    off, col, w = csr_from_edges(k, [(i, i + 1, i + 1) for i in range(k - 1)])
+    want = np.array([j * (j + 1) // 2 for j in range(k)], np.uint32)
+    for delta in (1, 3, 10, 100):
+        r = oracle.sssp_nearfar(off, col, w, 0, delta, 0)
+        np.testing.assert_array_equal(r.dist, want)
+        assert r.frontier_size.tolist() == [1] * k and r.relaxations == k - 1
+        # a split each time the next vertex lies above the current bucket: the buckets of d(1)..d(k-1)
+        # that differ from the bucket before them
+        buckets = [int(x) // delta for x in want]
+        assert r.splits == sum(1 for j in range(1, k) if buckets[j] != buckets[j - 1])
+
+
 def check_optimality(off, col, w, src, dist):
     """d(src)=0; d(v) <= d(u)+w on every edge out of a reached u; every reached
     v != src has an in-edge with equality; unreached vertices have no edge from a
