@@ -101,6 +101,8 @@ typedef struct dpc_tuning {
   int32_t chunk;          /* work per child unit: SpMV nnz (2048), PageRank in-edges (512), SSSP and colouring edges (256), BFS edges (256, at most), tree children (32; grid 16, queue 8) */
   int32_t kc;             /* X of KC_X; default 1 (grid), 16 (block), 32 (warp) */
   uint32_t flags;         /* DPC_FLAG_* */
+  int32_t delta;          /* dpc_sssp: near-far split width (0: no split; see dpc_sssp) */
+  int32_t sub_delta;      /* dpc_sssp: sub-split width for vertices above the threshold (0: none) */
 } dpc_tuning;
 
 /*
@@ -161,6 +163,18 @@ dpc_status dpc_device_init(int device, size_t pending_launch_limit);
  * Frontier rounds of relaxation: each frontier vertex with out-degree above
  * tuning.threshold hands its edge list to a child kernel at the given level.
  * Duplicate edges and self-loops are allowed.
+ *
+ * With tuning.delta > 0 the rounds use the near-far split of Davidson et al.
+ * (IPDPS 2014): a vertex whose distance dropped joins the next frontier only
+ * below the split distance S (a multiple of delta), else a far pile; when the
+ * frontier is empty, S moves to the delta-bucket above the smallest far
+ * distance still pending and the far vertices below it form the frontier.
+ * With tuning.sub_delta > 0 a frontier vertex above the threshold is relaxed
+ * only when its distance is below a sub-split s (a multiple of sub_delta,
+ * advanced the same way); until then it waits in the frontier. Both cut the
+ * edges relaxed more than once; distances are the same either way.
+ * stats->rounds counts relaxation rounds; a run that would exceed 2^32 - 16
+ * rounds (n + 1 without a split) ends with DPC_ERR_OVERFLOW.
  */
 dpc_status dpc_sssp_workspace_size(int32_t n, int32_t m, dpc_level level, const dpc_tuning *tuning, size_t *bytes);
 dpc_status dpc_sssp(const int32_t *off, const int32_t *col, const uint32_t *w, int32_t n, int32_t m, int32_t source,

@@ -52,7 +52,8 @@ def _bind(lib):
     lib.oracle_sssp_dijkstra.restype = ctypes.c_int
     lib.oracle_sssp_frontier.argtypes = [i32, P, P, P, i32, i32, P, i64, P, P, P]
     lib.oracle_sssp_frontier.restype = i64
-    lib.oracle_sssp_nearfar.argtypes = [i32, P, P, P, i32, ctypes.c_uint32, i32, P, i64, P, P, P, P]
+    lib.oracle_sssp_nearfar.argtypes = [i32, P, P, P, i32, ctypes.c_uint32, ctypes.c_uint32, i32, P, i64, P, P, P, P,
+                                        P]
     lib.oracle_sssp_nearfar.restype = i64
     lib.oracle_spmv_f64.argtypes = [i32, i32, P, P, P, P, P, P]
     lib.oracle_spmv_f64.restype = ctypes.c_int
@@ -137,27 +138,31 @@ def sssp_frontier(off, col, w, source: int, threshold: int, max_rounds: int = 1 
 @dataclass
 class NearFarRun(FrontierRun):
     splits: int = 0
+    subsplits: int = 0
 
 
-def sssp_nearfar(off, col, w, source: int, delta: int, threshold: int, max_rounds: int = 1 << 24) -> NearFarRun:
-    """Frontier rounds with the near-far split of width `delta` (0: no split)."""
+def sssp_nearfar(off, col, w, source: int, delta: int, threshold: int, sub_delta: int = 0,
+                 max_rounds: int = 1 << 24) -> NearFarRun:
+    """Frontier rounds with the near-far split of width `delta` (0: no split)
+    and, for vertices above the threshold, the sub-split of width `sub_delta`
+    (0: none)."""
     off, col, w = _c(off, np.int32), _c(col, np.int32), _c(w, np.uint32)
     n = off.shape[0] - 1
     dist = np.empty(n, np.uint32)
-    fs_list, hv_list = [], []
     cap = min(max_rounds, 1 << 16)
     while True:
         fs = np.zeros(cap, np.int64)
         hv = np.zeros(cap, np.int64)
-        relax, splits = ctypes.c_int64(0), ctypes.c_int64(0)
-        r = _load().oracle_sssp_nearfar(n, _p(off), _p(col), _p(w), source, int(delta), threshold, _p(dist), cap,
-                                        _p(fs), _p(hv), ctypes.addressof(relax), ctypes.addressof(splits))
+        relax, splits, subs = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        r = _load().oracle_sssp_nearfar(n, _p(off), _p(col), _p(w), source, int(delta), int(sub_delta), threshold,
+                                        _p(dist), cap, _p(fs), _p(hv), ctypes.addressof(relax),
+                                        ctypes.addressof(splits), ctypes.addressof(subs))
         if r >= 0 or cap >= max_rounds:
             break
         cap = min(max_rounds, cap * 16)  # more rounds than the arrays held: run again with room
     if r < 0:
         raise ValueError("oracle_sssp_nearfar failed")
-    return NearFarRun(dist, fs[:r].copy(), hv[:r].copy(), int(relax.value), int(splits.value))
+    return NearFarRun(dist, fs[:r].copy(), hv[:r].copy(), int(relax.value), int(splits.value), int(subs.value))
 
 
 def spmv_f64(off, col, val, x, ncols: int | None = None):

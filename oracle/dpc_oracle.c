@@ -199,45 +199,66 @@ int64_t oracle_sssp_frontier(int32_t n, const int32_t *off, const int32_t *col, 
  * Near-far frontier rounds: the rounds of oracle_sssp_frontier with the
  * near-far work split of Davidson, Baxter, Garland & Owens ("Work-Efficient
  * Parallel GPU Methods for Single-Source Shortest Paths", IPDPS 2014) put in
- * front of them. A split distance S, always a multiple of delta, divides the
- * vertices whose distance dropped in a round: those with d < S form the next
- * frontier (the near set), the others join the far pile (a set: a vertex is in
- * it at most once). A round is the Jacobi round of oracle_sssp_frontier on the
- * near set. When a round leaves the near set empty the split advances:
+ * front of them, and a finer split for heavy vertices.
+ *
+ * A split distance S, always a multiple of delta, divides the vertices whose
+ * distance dropped in a round: those with d < S join the near set, the others
+ * the far pile (a set: a vertex is in it at most once). A round relaxes part
+ * of the near set, Jacobi-style as in oracle_sssp_frontier (each relaxed
+ * vertex offers the distance it had when the round began).
+ *
+ * Which near vertices a round relaxes: a vertex whose out-degree is at most
+ * `threshold` always; a heavy one (out-degree above the threshold) only when
+ * its distance is below the sub-split s, a multiple of sub_delta; the other
+ * heavy ones stay in the near set for a later round. When no near vertex
+ * qualifies, s advances to sub_delta * (floor(hmin / sub_delta) + 1), hmin the
+ * smallest distance in the near set (a sub-split advance). sub_delta = 0: no
+ * sub-split (every near vertex qualifies).
+ *
+ * When the near set is empty the split advances:
  *   - far-pile vertices with d < S were relaxed with their current distance
  *     already (they dropped below S, so they went through the near set) and
  *     are dropped;
  *   - dmin = the smallest distance among the others; S becomes
- *     delta * (floor(dmin / delta) + 1), the top of dmin's bucket;
+ *     delta * (floor(dmin / delta) + 1), the top of dmin's bucket, and s
+ *     becomes sub_delta * (floor(dmin / sub_delta) + 1);
  *   - far-pile vertices with d < S (the new) leave the pile and form the near set.
  * The run ends when the near set and the far pile are both empty. delta = 0
- * means no split (S infinite): exactly the rounds of oracle_sssp_frontier.
+ * means no split (S infinite): with sub_delta = 0 too, exactly the rounds of
+ * oracle_sssp_frontier.
  *
- * Per round r: frontier_size[r] = near-set size, heavy[r] = its vertices with
- * out-degree above threshold. *relaxations = edges examined, *splits = split
- * advances. Returns the number of rounds, or -1 on bad arguments / more than
- * max_rounds rounds / distance overflow.
+ * Per round r: frontier_size[r] = vertices relaxed, heavy[r] = those of them
+ * with out-degree above the threshold. *relaxations = edges examined, *splits =
+ * split advances, *subsplits = sub-split advances. Returns the number of
+ * rounds, or -1 on bad arguments / more than max_rounds rounds / distance
+ * overflow.
  */
 int64_t oracle_sssp_nearfar(int32_t n, const int32_t *off, const int32_t *col, const uint32_t *w, int32_t source,
-                            uint32_t delta, int32_t threshold, uint32_t *dist_out, int64_t max_rounds,
-                            int64_t *frontier_size, int64_t *heavy, int64_t *relaxations, int64_t *splits) {
+                            uint32_t delta, uint32_t sub_delta, int32_t threshold, uint32_t *dist_out,
+                            int64_t max_rounds, int64_t *frontier_size, int64_t *heavy, int64_t *relaxations,
+                            int64_t *splits, int64_t *subsplits) {
   if (n < 1 || source < 0 || source >= n) return -1;
   uint64_t *d = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
   uint64_t *dprev = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
   int32_t *near = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *act = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   int32_t *changed = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   int32_t *far = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  uint8_t *in_near = (uint8_t *)calloc((size_t)n, 1);
   uint8_t *in_changed = (uint8_t *)calloc((size_t)n, 1);
   uint8_t *in_far = (uint8_t *)calloc((size_t)n, 1);
-  if (!d || !dprev || !near || !changed || !far || !in_changed || !in_far) {
-    free(d); free(dprev); free(near); free(changed); free(far); free(in_changed); free(in_far);
+  if (!d || !dprev || !near || !act || !changed || !far || !in_near || !in_changed || !in_far) {
+    free(d); free(dprev); free(near); free(act); free(changed); free(far); free(in_near); free(in_changed);
+    free(in_far);
     return -1;
   }
   for (int32_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
   d[source] = 0;
   uint64_t S = delta ? (uint64_t)delta : UINT64_MAX;
-  int64_t nnear = 1, nfar = 0, rounds = 0, relax = 0, nsplit = 0;
+  uint64_t s = sub_delta ? (uint64_t)sub_delta : UINT64_MAX;
+  int64_t nnear = 1, nfar = 0, rounds = 0, relax = 0, nsplit = 0, nsub = 0;
   near[0] = source;
+  in_near[source] = 1;
   int bad = 0;
   for (;;) {
     if (nnear == 0) {
@@ -253,26 +274,52 @@ int64_t oracle_sssp_nearfar(int32_t n, const int32_t *off, const int32_t *col, c
       }
       const uint64_t S_old = S;
       S = (dmin / delta + 1) * (uint64_t)delta;
+      if (sub_delta) s = (dmin / sub_delta + 1) * (uint64_t)sub_delta;
       nsplit++;
       int64_t keep = 0;
       for (int64_t i = 0; i < nfar; ++i) {
         int32_t v = far[i];
-        if (d[v] < S_old) { in_far[v] = 0; continue; }             /* relaxed already */
-        if (d[v] < S) { in_far[v] = 0; near[nnear++] = v; continue; } /* the new near set */
+        if (d[v] < S_old) { in_far[v] = 0; continue; } /* relaxed already */
+        if (d[v] < S) {                                 /* the new near set */
+          in_far[v] = 0;
+          near[nnear++] = v;
+          in_near[v] = 1;
+          continue;
+        }
         far[keep++] = v;
       }
       nfar = keep;
       continue;
     }
     if (rounds >= max_rounds) { bad = 1; break; }
-    int64_t hv = 0;
-    for (int64_t i = 0; i < nnear; ++i) if (off[near[i] + 1] - off[near[i]] > threshold) hv++;
-    frontier_size[rounds] = nnear;
-    heavy[rounds] = hv;
-    for (int64_t i = 0; i < nnear; ++i) dprev[near[i]] = d[near[i]];
-    int64_t nc = 0;
+    /* the near vertices this round relaxes */
+    int64_t na = 0;
     for (int64_t i = 0; i < nnear; ++i) {
-      int32_t u = near[i];
+      int32_t v = near[i];
+      if (off[v + 1] - off[v] <= threshold || d[v] < s) act[na++] = v;
+    }
+    if (na == 0) { /* only heavy vertices at or above the sub-split: advance it */
+      uint64_t hmin = UINT64_MAX;
+      for (int64_t i = 0; i < nnear; ++i) if (d[near[i]] < hmin) hmin = d[near[i]];
+      s = (hmin / sub_delta + 1) * (uint64_t)sub_delta;
+      nsub++;
+      for (int64_t i = 0; i < nnear; ++i) if (d[near[i]] < s) act[na++] = near[i];
+    }
+    /* the rest stay in the near set */
+    int64_t keep = 0;
+    for (int64_t i = 0, j = 0; i < nnear; ++i) {
+      if (j < na && near[i] == act[j]) { in_near[near[i]] = 0; j++; continue; }
+      near[keep++] = near[i];
+    }
+    nnear = keep;
+    int64_t hv = 0;
+    for (int64_t i = 0; i < na; ++i) if (off[act[i] + 1] - off[act[i]] > threshold) hv++;
+    frontier_size[rounds] = na;
+    heavy[rounds] = hv;
+    for (int64_t i = 0; i < na; ++i) dprev[act[i]] = d[act[i]];
+    int64_t nc = 0;
+    for (int64_t i = 0; i < na; ++i) {
+      int32_t u = act[i];
       for (int64_t e = off[u]; e < off[u + 1]; ++e) {
         int32_t v = col[e];
         uint64_t nd = dprev[u] + (uint64_t)w[e];
@@ -284,13 +331,16 @@ int64_t oracle_sssp_nearfar(int32_t n, const int32_t *off, const int32_t *col, c
       }
     }
     rounds++;
-    /* split the vertices that dropped into the next near set and the far pile */
-    nnear = 0;
+    /* the vertices that dropped: into the near set or the far pile */
     for (int64_t i = 0; i < nc; ++i) {
       int32_t v = changed[i];
       in_changed[v] = 0;
-      if (d[v] < S) near[nnear++] = v;
-      else if (!in_far[v]) { in_far[v] = 1; far[nfar++] = v; }
+      if (d[v] < S) {
+        if (!in_near[v]) { in_near[v] = 1; near[nnear++] = v; }
+      } else if (!in_far[v]) {
+        in_far[v] = 1;
+        far[nfar++] = v;
+      }
     }
   }
   for (int32_t v = 0; v < n; ++v) {
@@ -300,7 +350,9 @@ int64_t oracle_sssp_nearfar(int32_t n, const int32_t *off, const int32_t *col, c
   }
   *relaxations = relax;
   if (splits) *splits = nsplit;
-  free(d); free(dprev); free(near); free(changed); free(far); free(in_changed); free(in_far);
+  if (subsplits) *subsplits = nsub;
+  free(d); free(dprev); free(near); free(act); free(changed); free(far); free(in_near); free(in_changed);
+  free(in_far);
   return bad ? -1 : rounds;
 }
 

@@ -150,6 +150,9 @@ dpc_status resolve_static(const dpc_tuning *t, int def_chunk, LaunchCfg *c) {
   if (!valid_threads(c->parent_threads) || !valid_threads(c->child_threads)) return DPC_ERR_INVALID_ARG;
   if (c->chunk < 1 || c->chunk > (1 << 24) || t->parent_blocks < 0 || t->child_blocks < 0 || t->kc < 0)
     return DPC_ERR_INVALID_ARG;
+  if (t->delta < 0 || t->sub_delta < 0) return DPC_ERR_INVALID_ARG;
+  c->delta = (unsigned)t->delta;
+  c->sub_delta = (unsigned)t->sub_delta;
   return DPC_OK;
 }
 
@@ -215,7 +218,7 @@ const char *dpc_status_string(dpc_status s) {
   return "unknown dpc_status";
 }
 
-int32_t dpc_abi_version(void) { return 1; }
+int32_t dpc_abi_version(void) { return 2; }
 
 dpc_status dpc_device_init(int device, size_t pending_launch_limit) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -600,21 +603,13 @@ dpc_status dpc_sssp(const int32_t *off, const int32_t *col, const uint32_t *w, i
   p.child_threads = c.child_threads;
   p.heap = (c.flags & DPC_FLAG_DEVICE_MALLOC) && (level == DPC_WARP || level == DPC_BLOCK) ? 1 : 0;
   p.stream_edges = (size_t)m * (sizeof(int) + sizeof(unsigned)) > l2_bytes(dev) / 2 ? 1 : 0;
+  p.delta = c.delta;
+  p.sub_delta = c.sub_delta;
+  // Without a split the frontier of round n is empty (Bellman-Ford's bound);
+  // with one, the cap only keeps the round stamps below their sentinel.
+  p.max_rounds = (c.delta || c.sub_delta) ? 0xFFFFFFF0u : (unsigned)n + 1u;
   p.launch_budget = launch_budget(dev);
-  char *b = static_cast<char *>(workspace);
-  p.hdr = reinterpret_cast<WsHeader *>(b);
-  b += kHeaderBytes;
-  p.fcur = reinterpret_cast<int2 *>(b);
-  b += align_up((size_t)n * sizeof(int2), 256);
-  p.fnext = reinterpret_cast<int *>(b);
-  b += align_up((size_t)n * sizeof(int), 256);
-  p.stamp = reinterpret_cast<unsigned *>(b);
-  b += align_up((size_t)n * sizeof(unsigned), 256);
-  if (level == DPC_WARP || level == DPC_BLOCK || level == DPC_GRID || level == DPC_QUEUE) {
-    const size_t mu = sssp_max_units(n, m, c.threshold, c.chunk);
-    p.units = reinterpret_cast<int4 *>(b);
-    p.max_units = (int)(mu > (size_t)INT_MAX ? INT_MAX : mu);
-  }
+  sssp_carve(p, workspace, n, m, level, c);
   p.stats = stats;
   if (level == DPC_QUEUE) {
     // one cooperative grid: every block co-resident (occupancy with the staging buffers)

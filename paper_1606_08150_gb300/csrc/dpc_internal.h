@@ -18,20 +18,43 @@ struct LaunchCfg {
   int child_threads;
   int chunk;
   unsigned flags;
+  unsigned delta;      // SSSP near-far split width (0: none)
+  unsigned sub_delta;  // SSSP sub-split width for heavy vertices (0: none)
 };
 
 // Workspace header: counters that every call zeroes before its first kernel.
+// Counters that many warps update in the same phase, and the word that the
+// blocks of a grid barrier poll, sit on cache lines of their own: atomics on
+// one line serialise in one L2 slice, and polls of a line slow its atomics.
 struct WsHeader {
-  unsigned long long cursor;   // units reserved in the current buffer
-  unsigned long long cursor2;  // second list (SSSP next frontier, tree next level)
-  unsigned done_blocks;        // last-block-done ticket counter
+  // line 0: arrivals at the grid barriers (last-block tickets, multi-use barriers)
+  unsigned done_blocks;
   unsigned done_blocks2;
-  unsigned status;             // device status (dpc_status numbering)
-  unsigned round;              // SSSP round / tree level reached
-  unsigned long long launches; // optional device launches attempted (checked against the budget)
-  unsigned long long aux[4];
+  // line 1: the release word the waiting blocks poll, the status, the launch counter
+  alignas(128) unsigned round;   // SSSP round / tree level reached; release word of the queue barriers
+  unsigned status;               // device status (dpc_status numbering)
+  unsigned long long launches;   // optional device launches attempted (checked against the budget)
+  // line 2: units reserved in the current buffer
+  alignas(128) unsigned long long cursor;
+  // line 3: second list (SSSP next frontier, tree next level)
+  alignas(128) unsigned long long cursor2;
+  // line 4: per-application words (frontier size, snapshots, the child's unit cursor)
+  alignas(128) unsigned long long aux[4];
+  // line 5: SSSP commit counters (near-far split)
+  alignas(128) unsigned long long nf_near;  // entries of the next frontier (the near set) written so far
+  unsigned long long nf_elig;               // of those, the ones the next round relaxes
+  unsigned nf_hmin;                         // smallest distance of a heavy near vertex that waits
+  // line 6: far-pile appends (during the relaxations)
+  alignas(128) unsigned long long nf_far[2];  // far pile sizes: the current list and the other
+  // line 7: the split (read by every phase, written between phases)
+  alignas(128) unsigned nf_split;             // split distance S (all ones: no split; finite distances are below it)
+  unsigned nf_sub;                            // sub-split distance s for heavy vertices (all ones: none)
+  unsigned nf_split_old;                      // S before the split in progress
+  unsigned nf_dmin;                           // smallest live far-pile distance (split in progress)
+  unsigned nf_epoch;                          // far-pile epoch: a vertex is in the pile when its mark equals it
+  unsigned nf_cur;                            // index of the current far list
 };
-constexpr size_t kHeaderBytes = 256;
+constexpr size_t kHeaderBytes = 1024;
 static_assert(sizeof(WsHeader) <= kHeaderBytes, "workspace header too large");
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -42,6 +65,7 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // them later then writes and reads live memory, never a returned stack frame.
 struct HostScratch {
   unsigned long long count;
+  unsigned long long sizes[3];
   int value;
   unsigned rounds;
 };
@@ -206,16 +230,24 @@ struct SsspParams {
   int max_units;
   int heap;           // 1: warp and block buffers come from the device heap (DPC_FLAG_DEVICE_MALLOC)
   int stream_edges;   // 1: col/w larger than half of L2, read with the evict-first hint
+  unsigned delta;     // near-far split width (0: no split)
+  unsigned sub_delta; // sub-split width for vertices above the threshold (0: none)
+  unsigned max_rounds;
   long long launch_budget;
-  int2 *fcur;         // frontier of the current round: (vertex, distance when the round began)
-  int *fnext;         // vertices whose distance dropped in the current round
+  int4 *fcur;         // frontier of the current round: (vertex, distance when the round began,
+                      // first edge, end edge)
+  int *fnext;         // vertices whose distance dropped in the round, and heavy ones that wait
   unsigned *stamp;    // last round in which a vertex entered fnext
-  int4 *units;        // (vertex, chunk index, distance of the vertex, 0)
-  WsHeader *hdr;      // cursor: units; cursor2: |fnext|; aux[0]: |fcur|
+  int *far[2];        // far piles (near-far split only)
+  unsigned *fmark;    // far-pile epoch of each vertex (near-far split only)
+  int4 *units;        // (first edge, end edge, distance of the vertex, vertex)
+  WsHeader *hdr;      // cursor: units; cursor2: |fnext|; aux[0]: |fcur|; nf_*: the split
   dpc_stats *stats;
 };
 
 size_t sssp_workspace_bytes(int n, int m, dpc_level level, const LaunchCfg &c);
+// Points the frontier, stamp, far-pile and unit arrays of p (and p.hdr) into the workspace.
+void sssp_carve(SsspParams &p, void *workspace, int n, int m, dpc_level level, const LaunchCfg &c);
 size_t sssp_max_units(int n, int m, int threshold, int chunk);
 // Launches the whole call on `s`; the flat level drives its rounds from the host.
 cudaError_t sssp_launch(SsspParams &p, dpc_level level, cudaStream_t s, unsigned *rounds_out);

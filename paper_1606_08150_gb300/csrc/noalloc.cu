@@ -114,6 +114,8 @@ extern "C" dpc_status dpc_spmv_csr_noalloc(const int32_t *off, const int32_t *co
   c.flags = t->flags;
   c.parent_blocks = t->parent_blocks;
   c.child_blocks = t->child_blocks;
+  c.delta = 0;
+  c.sub_delta = 0;
   for (int th : {c.parent_threads, c.child_threads})
     if (th < 32 || th > 1024 || th % 32) return DPC_ERR_INVALID_ARG;
   if (c.chunk < 1 || c.chunk > (1 << 24) || t->parent_blocks < 0 || t->child_blocks < 0 || t->kc < 0)

@@ -1,25 +1,43 @@
-// Single-source shortest paths at the five consolidation levels.
+// Single-source shortest paths at the five consolidation levels and the queue level.
 //
 // The SSSP kernel of Fig. 1b, applied round after round: every vertex of the
 // frontier relaxes its out-edges; a vertex whose out-degree exceeds
 // `threshold` is large work. The rounds are Jacobi-style: round r relaxes with
-// the distances that the frontier vertices had when the round began (kept next
-// to each frontier entry), so the set of vertices entering the next frontier -
+// the distances that the frontier vertices had when the round began (kept in
+// each frontier entry), so the set of vertices entering the next frontier -
 // and with it every launch count - is independent of the order in which the
 // relaxations of a round happen.
 //
-// One round on the device (every level but flat):
+// Optionally the rounds follow the near-far work split of Davidson, Baxter,
+// Garland & Owens (IPDPS 2014): a split distance S (a multiple of `delta`)
+// sends vertices that dropped to d >= S to a far pile instead of the next
+// frontier; when the frontier runs empty, S moves to the bucket above the
+// smallest live far distance and those far vertices form the next frontier.
+// A finer sub-split s (a multiple of `sub_delta`) holds heavy frontier
+// vertices (above the threshold) back while their distance is not below s, so
+// that a hub is relaxed once its distance has settled instead of on every
+// drop. Without a split every vertex that dropped is in the next frontier.
+//
+// One round on the device (every level but flat and queue):
 //   parent(r)   block 0 first tail-launches commit(r); threads relax short
 //               frontier vertices inline and hand long ones to a child
 //               (basic-DP: one child per vertex; warp/block/grid: units of
 //               `chunk` edges appended to a consolidation buffer and one
-//               consolidated child per warp/block/grid, Sec. IV.B-C).
+//               consolidated child per warp/block/grid, Sec. IV.B-C); heavy
+//               vertices held back by the sub-split wait for a later round.
 //   commit(r)   runs after parent(r) and all its children (CDP2 tail launch,
 //               the device-side replacement for the cudaDeviceSynchronize of
-//               Sec. IV.C); it snapshots (vertex, distance) for the next
-//               frontier and its last block tail-launches parent(r+1).
-// The flat level runs the same two kernels from a host loop, reading the
-// frontier size back after every round.
+//               Sec. IV.C); it writes the next frontier's entries (vertex,
+//               distance, edge range), sends far vertices to the far pile, and
+//               its last block tail-launches parent(r+1), or - when the
+//               frontier is empty and the far pile is not - the split.
+//   split       split_min (smallest live far distance, the new S and s), then
+//               split_apply (far vertices below the new S become the
+//               frontier, the others move to the second far list), whose last
+//               block tail-launches parent(r+1).
+// The flat level runs the same kernels from a host loop, reading the frontier
+// and far-pile sizes back after every step; the queue level runs every phase
+// in one cooperative grid, separated by grid barriers.
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
@@ -33,10 +51,55 @@ namespace dpc {
 namespace {
 
 constexpr unsigned kInf = 0xFFFFFFFFu;
+constexpr unsigned kNoSplit = 0xFFFFFFFFu;  // a split distance above every finite distance
 
 __device__ __forceinline__ void sssp_fail(const SsspParams &p, unsigned code) {
   set_status(&p.hdr->status, code);
   if (p.stats) atomicCAS(&p.stats->status, 0u, code);
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_volatile(const T *a) {
+  return *reinterpret_cast<const volatile T *>(a);
+}
+
+// The state of the running phase: read from the workspace header once per
+// block (by thread 0, at kernel start or after a grid barrier) and kept in
+// shared memory, since every warp reading the same header words from L2 after
+// each barrier serialises in one L2 slice.
+struct Phase {
+  unsigned long long nf;     // frontier entries of the round (aux[0])
+  unsigned long long aux1;   // queue level: entries of the round's list, published after the children
+  unsigned long long next;   // entries of the round's list so far (cursor2)
+  unsigned long long units;  // units in the buffer
+  unsigned long long nfar;   // entries of the current far list
+  unsigned S;                // split distance: below it a vertex that dropped joins the next frontier
+  unsigned s;                // sub-split: a heavy frontier vertex is relaxed below it
+  unsigned S_old;            // (split in progress) far vertices below it are stale
+  unsigned cur;              // current far list
+  unsigned epoch;            // far-pile epoch
+};
+__shared__ Phase s_ph;
+
+__device__ __forceinline__ void phase_load(const SsspParams &p) {
+  const WsHeader *h = p.hdr;
+  s_ph.nf = ld_volatile(&h->aux[0]);
+  s_ph.aux1 = ld_volatile(&h->aux[1]);
+  s_ph.next = ld_volatile(&h->cursor2);
+  s_ph.units = ld_volatile(&h->cursor);
+  s_ph.S = ld_volatile(&h->nf_split);
+  s_ph.s = ld_volatile(&h->nf_sub);
+  s_ph.S_old = ld_volatile(&h->nf_split_old);
+  s_ph.epoch = ld_volatile(&h->nf_epoch);
+  const unsigned cur = ld_volatile(&h->nf_cur);
+  s_ph.cur = cur;
+  s_ph.nfar = ld_volatile(&h->nf_far[cur]);
+}
+
+// Every thread of the block; at the start of a device-launched kernel.
+__device__ __forceinline__ void phase_sync(const SsspParams &p) {
+  if (threadIdx.x == 0) phase_load(p);
+  __syncthreads();
 }
 
 // v enters the next frontier once per round (stamp dedup); warp-aggregated append.
@@ -49,7 +112,29 @@ __device__ __forceinline__ void push_next(const SsspParams &p, int v, unsigned r
   p.fnext[base + g.thread_rank()] = v;
 }
 
-__device__ __forceinline__ void relax(const SsspParams &p, int v, unsigned du, unsigned w, unsigned r) {
+// v (whose distance dropped to S or more) joins the far pile once per epoch;
+// warp-aggregated append to the current far list.
+__device__ __forceinline__ void push_far(const SsspParams &p, int v) {
+  const unsigned epoch = s_ph.epoch;
+  if (atomicExch(p.fmark + v, epoch) == epoch) return;
+  const unsigned cur = s_ph.cur;
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&p.hdr->nf_far[cur], (unsigned long long)g.size());
+  base = g.shfl(base, 0);
+  p.far[cur][base + g.thread_rank()] = v;
+}
+
+// Where a vertex whose distance dropped to d goes: the next frontier below the
+// split S (once per round), else the far pile. A vertex that drops first to
+// S or more and later in the same round below S is in both; its far entry is
+// stale and the split drops it (its distance is below the old split by then).
+__device__ __forceinline__ void push_dropped(const SsspParams &p, int v, unsigned d, unsigned r, unsigned S) {
+  if (d < S) push_next(p, v, r);
+  else push_far(p, v);
+}
+
+__device__ __forceinline__ void relax(const SsspParams &p, int v, unsigned du, unsigned w, unsigned r, unsigned S) {
   const unsigned long long nd = (unsigned long long)du + w;
   if (nd >= kInf) {
     sssp_fail(p, DPC_ERR_OVERFLOW);
@@ -57,8 +142,8 @@ __device__ __forceinline__ void relax(const SsspParams &p, int v, unsigned du, u
   }
   const unsigned d = (unsigned)nd;
   if (d < __ldcg(p.dist + v)) {
-    const unsigned old = atomicMin(p.dist + v, d);
-    if (d < old) push_next(p, v, r);
+    atomicMin(p.dist + v, d);  // result unused: a reduction, no round trip (see relax_batch)
+    push_dropped(p, v, d, r, S);
   }
 }
 
@@ -80,8 +165,59 @@ __device__ __forceinline__ unsigned edge_w(const SsspParams &p, int e) {
   return p.stream_edges ? __ldcs(p.w + e) : __ldg(p.w + e);
 }
 
-__device__ __forceinline__ void relax_edges(const SsspParams &p, int a, int b, unsigned du, unsigned r, int t,
-                                            int T) {
+// One batch of up to kRelaxBatch edges per lane: v[j] targets, d[j] offered
+// distances (kInf: none). Returns the mask of entries that entered the next
+// frontier (fresh in this round); entries that dropped to S or more went to
+// the far pile.
+//
+// An offer below the distance read here drops the target's distance in this
+// round whoever's atomicMin lands first (the value read is at most the one
+// the round began with), so the target belongs to the next frontier either
+// way: the atomicMin needs no result and is issued as a reduction, and the
+// round stamp alone keeps the target from entering the list twice.
+__device__ __forceinline__ unsigned relax_batch(const SsspParams &p, const int (&v)[kRelaxBatch],
+                                                const unsigned (&d)[kRelaxBatch], unsigned r, unsigned S) {
+  unsigned cur[kRelaxBatch];
+#pragma unroll
+  for (int j = 0; j < kRelaxBatch; ++j) cur[j] = (v[j] >= 0 && d[j] != kInf) ? __ldcg(p.dist + v[j]) : 0u;
+  unsigned improved = 0;
+#pragma unroll
+  for (int j = 0; j < kRelaxBatch; ++j)
+    if (d[j] < cur[j]) {
+      atomicMin(p.dist + v[j], d[j]);
+      improved |= 1u << j;
+    }
+  unsigned fresh = 0;
+#pragma unroll
+  for (int j = 0; j < kRelaxBatch; ++j) {
+    if (!(improved >> j & 1u)) continue;
+    if (d[j] < S) {
+      if (atomicExch(p.stamp + v[j], r) != r) fresh |= 1u << j;
+    } else {
+      push_far(p, v[j]);
+    }
+  }
+  return fresh;
+}
+
+// In the full-warp loops adjacent lanes hold adjacent edges. An edge whose
+// target is the previous lane's and whose offer is not lower adds nothing
+// (the previous lane's offer, or a lower one before it, is relaxed), so it is
+// dropped before the atomics. Duplicate edges are adjacent in a CSR sorted by
+// target, and an R-MAT hub holds thousands of them: without this their
+// atomicMin on one address serialise.
+__device__ __forceinline__ void drop_adjacent_duplicates(const int (&v)[kRelaxBatch], unsigned (&d)[kRelaxBatch]) {
+  const bool first = lane_id() == 0;
+#pragma unroll
+  for (int j = 0; j < kRelaxBatch; ++j) {
+    const int pv = __shfl_up_sync(0xffffffffu, v[j], 1);
+    const unsigned pd = __shfl_up_sync(0xffffffffu, d[j], 1);
+    if (!first && pv == v[j] && pd <= d[j]) d[j] = kInf;
+  }
+}
+
+__device__ __forceinline__ void relax_edges(const SsspParams &p, int a, int b, unsigned du, unsigned r, unsigned S,
+                                            int t, int T) {
   for (int e0 = a + t; e0 < b; e0 += kRelaxBatch * T) {
     int v[kRelaxBatch];
     unsigned d[kRelaxBatch];
@@ -97,17 +233,7 @@ __device__ __forceinline__ void relax_edges(const SsspParams &p, int a, int b, u
         else d[j] = (unsigned)nd;
       }
     }
-    unsigned cur[kRelaxBatch];
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j) cur[j] = (v[j] >= 0 && d[j] != kInf) ? __ldcg(p.dist + v[j]) : 0u;
-    unsigned improved = 0;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if (d[j] < cur[j] && d[j] < atomicMin(p.dist + v[j], d[j])) improved |= 1u << j;
-    unsigned fresh = 0;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if ((improved >> j & 1u) && atomicExch(p.stamp + v[j], r) != r) fresh |= 1u << j;
+    const unsigned fresh = relax_batch(p, v, d, r, S);
     const int cnt = __popc(fresh);
     cg::coalesced_group g = cg::coalesced_threads();
     const int excl = cg::exclusive_scan(g, cnt);
@@ -154,9 +280,26 @@ __host__ __device__ __forceinline__ size_t stage_bytes(int threads) {
   return (size_t)(threads / kWarp) * (kStage + 1) * sizeof(int);
 }
 
+// A full warp stages the fresh vertices of one batch (every lane calls it).
+__device__ __forceinline__ void stage_batch(const SsspParams &p, const WarpStage &ws, unsigned fresh,
+                                            const int (&v)[kRelaxBatch]) {
+  const int cnt = __popc(fresh);
+  const int inc = warp_inclusive_scan(cnt);
+  const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
+  if (total == 0) return;
+  if (*ws.cnt + total > kStage) stage_flush(p, ws);
+  int pos = *ws.cnt + inc - cnt;
+#pragma unroll
+  for (int j = 0; j < kRelaxBatch; ++j)
+    if (fresh >> j & 1u) ws.buf[pos++] = v[j];
+  __syncwarp();
+  if (lane_id() == kWarp - 1) *ws.cnt += total;
+  __syncwarp();
+}
+
 // relax_edges for a full warp (t = lane, T = 32) with staged appends
 __device__ __forceinline__ void relax_edges_staged(const SsspParams &p, int a, int b, unsigned du, unsigned r,
-                                                   const WarpStage &ws) {
+                                                   unsigned S, const WarpStage &ws) {
   const int t = lane_id(), T = kWarp;
   for (int e0 = a + t; e0 - t < b; e0 += kRelaxBatch * T) {
     int v[kRelaxBatch];
@@ -173,107 +316,225 @@ __device__ __forceinline__ void relax_edges_staged(const SsspParams &p, int a, i
         else d[j] = (unsigned)nd;
       }
     }
-    unsigned cur[kRelaxBatch];
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j) cur[j] = (v[j] >= 0 && d[j] != kInf) ? __ldcg(p.dist + v[j]) : 0u;
-    unsigned improved = 0;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if (d[j] < cur[j] && d[j] < atomicMin(p.dist + v[j], d[j])) improved |= 1u << j;
-    unsigned fresh = 0;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if ((improved >> j & 1u) && atomicExch(p.stamp + v[j], r) != r) fresh |= 1u << j;
-    const int cnt = __popc(fresh);
-    const int inc = warp_inclusive_scan(cnt);
-    const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
-    if (total == 0) continue;
-    if (*ws.cnt + total > kStage) stage_flush(p, ws);
-    int pos = *ws.cnt + inc - cnt;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if (fresh >> j & 1u) ws.buf[pos++] = v[j];
-    __syncwarp();
-    if (t == kWarp - 1) *ws.cnt += total;
-    __syncwarp();
+    drop_adjacent_duplicates(v, d);
+    stage_batch(p, ws, relax_batch(p, v, d, r, S), v);
   }
 }
 
-// Inline work of the lanes of a full warp, each on its own short vertex (edges
-// [a, b) of the calling lane when `active`), eight consecutive edges per lane
-// and batch, in a loop that every lane of the warp runs the same number of
-// times so that new frontier vertices can be staged per warp.
-__device__ __forceinline__ void relax_inline_staged(const SsspParams &p, int a, int b, unsigned du, unsigned r,
-                                                    bool active, const WarpStage &ws) {
-  const int nb = active ? (b - a + kRelaxBatch - 1) / kRelaxBatch : 0;
-  const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)nb);
-  for (int k = 0; k < kmax; ++k) {
+// Inline work of a full warp over the short vertices of its lanes (edges
+// [a, b) of the calling lane when `active`): the lanes' edge lists are
+// concatenated and dealt out evenly, eight edges per lane and batch, adjacent
+// lanes on adjacent edges, so the warp needs ceil(sum of degrees / 256)
+// batches instead of as many as its longest vertex has. An edge's vertex is
+// the last lane whose exclusive prefix of degrees is not above the edge's
+// position (a five-step search over the warp's prefix sums).
+__device__ __forceinline__ void relax_inline_warp(const SsspParams &p, int a, int b, unsigned du, unsigned r,
+                                                  unsigned S, bool active, const WarpStage &ws) {
+  const int lane = lane_id();
+  const int deg = active ? b - a : 0;
+  const int incl = warp_inclusive_scan(deg);
+  const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+  const int excl = incl - deg;
+  for (int base = 0; base < total; base += kWarp * kRelaxBatch) {
     int v[kRelaxBatch];
     unsigned d[kRelaxBatch];
 #pragma unroll
     for (int j = 0; j < kRelaxBatch; ++j) {
-      const int e = a + k * kRelaxBatch + j;
+      const int k = base + j * kWarp + lane;
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int m = owner + step;
+        if (__shfl_sync(0xffffffffu, excl, m) <= k) owner = m;
+      }
+      const int e = __shfl_sync(0xffffffffu, a, owner) + k - __shfl_sync(0xffffffffu, excl, owner);
+      const unsigned dl = __shfl_sync(0xffffffffu, du, owner);
       v[j] = -1;
       d[j] = kInf;
-      if (k < nb && e < b) {
-        const unsigned long long nd = (unsigned long long)du + edge_w(p, e);
+      if (k < total) {
+        const unsigned long long nd = (unsigned long long)dl + edge_w(p, e);
         v[j] = edge_col(p, e);
         if (nd >= kInf) sssp_fail(p, DPC_ERR_OVERFLOW);
         else d[j] = (unsigned)nd;
       }
     }
-    unsigned cur[kRelaxBatch];
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j) cur[j] = (v[j] >= 0 && d[j] != kInf) ? __ldcg(p.dist + v[j]) : 0u;
-    unsigned improved = 0;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if (d[j] < cur[j] && d[j] < atomicMin(p.dist + v[j], d[j])) improved |= 1u << j;
-    unsigned fresh = 0;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if ((improved >> j & 1u) && atomicExch(p.stamp + v[j], r) != r) fresh |= 1u << j;
-    const int cnt = __popc(fresh);
-    const int inc = warp_inclusive_scan(cnt);
-    const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
-    if (total == 0) continue;
-    if (*ws.cnt + total > kStage) stage_flush(p, ws);
-    int pos = *ws.cnt + inc - cnt;
-#pragma unroll
-    for (int j = 0; j < kRelaxBatch; ++j)
-      if (fresh >> j & 1u) ws.buf[pos++] = v[j];
-    __syncwarp();
-    if (lane_id() == kWarp - 1) *ws.cnt += total;
-    __syncwarp();
+    drop_adjacent_duplicates(v, d);
+    stage_batch(p, ws, relax_batch(p, v, d, r, S), v);
   }
 }
 
 // All edges of u by one thread, in order (inline work of a parent thread).
-__device__ __forceinline__ void relax_all(const SsspParams &p, int a, int b, unsigned du, unsigned r) {
-  relax_edges(p, a, b, du, r, 0, 1);
+__device__ __forceinline__ void relax_all(const SsspParams &p, int a, int b, unsigned du, unsigned r, unsigned S) {
+  relax_edges(p, a, b, du, r, S, 0, 1);
 }
 
-// Edges [a, b) of one vertex by member t of a group of T threads.
-__device__ __forceinline__ void relax_group(const SsspParams &p, int a, int b, unsigned du, unsigned r, int t,
-                                            int T) {
-  relax_edges(p, a, b, du, r, t, T);
-}
-
-__device__ __forceinline__ void sssp_unit(const SsspParams &p, int4 u, unsigned r) {
-  if (u.x < 0) return;  // placeholder written after a buffer overflow
-  const int a0 = __ldg(p.off + u.x), b0 = __ldg(p.off + u.x + 1);
-  const int a = a0 + u.y * p.chunk;
-  const int b = min(b0, a + p.chunk);
-  relax_group(p, a, b, (unsigned)u.z, r, lane_id(), kWarp);
-}
-
+// A unit: (first edge, end edge, distance of its vertex, vertex); a unit whose
+// range is empty is a placeholder written after a buffer overflow.
 __device__ __forceinline__ void sssp_units_by_group(const SsspParams &p, const int4 *units, int lo, int hi,
-                                                    int warp_in_group, int warps_in_group, unsigned r) {
-  for (int u = lo + warp_in_group; u < hi; u += warps_in_group) sssp_unit(p, units[u], r);
+                                                    int warp_in_group, int warps_in_group, unsigned r, unsigned S) {
+  for (int u = lo + warp_in_group; u < hi; u += warps_in_group) {
+    const int4 un = units[u];
+    relax_edges(p, un.x, un.y, (unsigned)un.z, r, S, lane_id(), kWarp);
+  }
 }
 
-__device__ __forceinline__ int frontier_size(const SsspParams &p) {
-  return (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->aux[0]);
+
+
+// The split state every thread of a phase reads once (it changes only between phases).
+struct Split {
+  unsigned S;      // near: distance below S
+  unsigned s;      // a heavy near vertex is relaxed when its distance is below s
+  unsigned S_old;  // (split in progress) far vertices below it are stale
+  unsigned cur;    // current far list
+};
+
+__device__ __forceinline__ Split read_split() {
+  Split q;
+  q.S = s_ph.S;
+  q.s = s_ph.s;
+  q.S_old = s_ph.S_old;
+  q.cur = s_ph.cur;
+  return q;
+}
+
+// Does the next round relax this frontier entry? Light vertices always; a
+// heavy one only below the sub-split.
+__device__ __forceinline__ bool relaxed_now(const SsspParams &p, const int4 &f, unsigned s) {
+  return f.w - f.z <= p.threshold || (unsigned)f.y < s;
+}
+
+// A full warp appends the lanes with `near` set to the next frontier: entry
+// (v, d, first edge, end edge) at a warp-reserved slot, and accounts for the
+// next round: how many entries it relaxes, and the smallest distance of a
+// heavy entry that waits.
+__device__ __forceinline__ void append_near(const SsspParams &p, bool near, int v, unsigned dv, int a, int b,
+                                            unsigned s) {
+  const unsigned nb = __ballot_sync(0xffffffffu, near);
+  if (nb == 0) return;
+  unsigned long long base = 0;
+  if (lane_id() == 0) base = atomicAdd(&p.hdr->nf_near, (unsigned long long)__popc(nb));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const int4 f = make_int4(v, (int)dv, a, b);
+  const bool now = near && relaxed_now(p, f, s);
+  if (near) p.fcur[base + __popc(nb & lanemask_lt())] = f;
+  const unsigned eb = __ballot_sync(0xffffffffu, now);
+  if (eb == nb) {
+    if (lane_id() == 0) atomicAdd(&p.hdr->nf_elig, (unsigned long long)__popc(eb));
+    return;
+  }
+  const unsigned hm = __reduce_min_sync(0xffffffffu, (near && !now) ? dv : kInf);
+  if (lane_id() == 0) {
+    if (eb) atomicAdd(&p.hdr->nf_elig, (unsigned long long)__popc(eb));
+    atomicMin(&p.hdr->nf_hmin, hm);
+  }
+}
+
+// A full warp appends the lanes with `far` set to far list `list` (each lane's
+// vertex is new to that list).
+__device__ __forceinline__ void append_far(const SsspParams &p, bool far, int v, unsigned list) {
+  const unsigned fb = __ballot_sync(0xffffffffu, far);
+  if (fb == 0) return;
+  unsigned long long base = 0;
+  if (lane_id() == 0) base = atomicAdd(&p.hdr->nf_far[list], (unsigned long long)__popc(fb));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (far) p.far[list][base + __popc(fb & lanemask_lt())] = v;
+}
+
+// Commit of one entry of the round's list (called by full warps; `valid`
+// false for lanes past the end): every listed vertex is below the split (the
+// relaxations sent the others to the far pile), so it becomes a next-frontier
+// entry with the distance and edge range it has now.
+__device__ __forceinline__ void commit_vertex(const SsspParams &p, bool valid, int v, const Split &q) {
+  unsigned dv = kInf;
+  int a = 0, b = 0;
+  if (valid) {
+    dv = __ldcg(p.dist + v);
+    a = __ldg(p.off + v);
+    b = __ldg(p.off + v + 1);
+  }
+  append_near(p, valid, v, dv, a, b, q.s);
+}
+
+// Split, first pass: the smallest distance among far-pile vertices at or
+// above S (the others were relaxed with their distance already).
+__device__ __forceinline__ void split_min_vertex(const SsspParams &p, bool valid, int v, const Split &q) {
+  unsigned dv = kInf;
+  if (valid) {
+    dv = __ldcg(p.dist + v);
+    if (dv < q.S) dv = kInf;
+  }
+  const unsigned m = __reduce_min_sync(0xffffffffu, dv);
+  if (lane_id() == 0 && m != kInf) atomicMin(&p.hdr->nf_dmin, m);
+}
+
+// Split, second pass (S and s are the new ones): stale far vertices (below the
+// old S) leave the pile, those below the new S form the next frontier, the
+// rest move to the other far list with the next epoch's mark.
+__device__ __forceinline__ void split_apply_vertex(const SsspParams &p, bool valid, int v, const Split &q,
+                                                   unsigned epoch) {
+  unsigned dv = kInf;
+  int a = 0, b = 0;
+  if (valid) {
+    dv = __ldcg(p.dist + v);
+    a = __ldg(p.off + v);
+    b = __ldg(p.off + v + 1);
+  }
+  const bool live = valid && dv >= q.S_old;
+  const bool near = live && dv < q.S;
+  append_near(p, near, v, dv, a, b, q.s);
+  const bool keep = live && !near;
+  if (keep) p.fmark[v] = epoch + 1;
+  append_far(p, keep, v, q.cur ^ 1u);
+}
+
+// The top of the width-w bucket of distance d, at most all ones.
+__device__ __forceinline__ unsigned bucket_top(unsigned d, unsigned w) {
+  const unsigned long long t = ((unsigned long long)d / w + 1) * (unsigned long long)w;
+  return t < kNoSplit ? (unsigned)t : kNoSplit;
+}
+
+// Make the near set written by a commit or a split the next round's frontier
+// (single thread, after every block has finished the phase). When none of its
+// entries would be relaxed (only heavy vertices at or above the sub-split),
+// the sub-split first moves to the top of the smallest one's sub-bucket.
+__device__ __forceinline__ void publish_frontier(const SsspParams &p) {
+  WsHeader *h = p.hdr;
+  const unsigned long long nn = ld_volatile(&h->nf_near);
+  if (nn > 0 && ld_volatile(&h->nf_elig) == 0 && p.sub_delta) h->nf_sub = bucket_top(ld_volatile(&h->nf_hmin), p.sub_delta);
+  h->aux[0] = nn;
+  h->nf_near = 0ull;
+  h->nf_elig = 0ull;
+  h->nf_hmin = kInf;
+  h->cursor2 = 0ull;
+  h->cursor = 0ull;
+  h->aux[2] = 0ull;    // the grid-level child's unit cursor
+  h->launches = 0ull;  // the round's children have all finished: their pool slots are free
+}
+
+// The split's new S and s from the smallest live far distance (single
+// thread). Returns false when every far vertex was stale (the pile empties).
+__device__ __forceinline__ bool advance_split(const SsspParams &p) {
+  WsHeader *h = p.hdr;
+  const unsigned dmin = ld_volatile(&h->nf_dmin);
+  h->nf_dmin = kInf;
+  if (dmin == kInf) {
+    h->nf_far[ld_volatile(&h->nf_cur)] = 0ull;
+    return false;
+  }
+  h->nf_split_old = ld_volatile(&h->nf_split);
+  h->nf_split = bucket_top(dmin, p.delta);
+  if (p.sub_delta) h->nf_sub = bucket_top(dmin, p.sub_delta);
+  return true;
+}
+
+// After split_apply: the other far list becomes the current one, the epoch advances.
+__device__ __forceinline__ void finish_split(const SsspParams &p) {
+  WsHeader *h = p.hdr;
+  const unsigned cur = ld_volatile(&h->nf_cur);
+  h->nf_far[cur] = 0ull;
+  h->nf_cur = cur ^ 1u;
+  h->nf_epoch = ld_volatile(&h->nf_epoch) + 1u;
+  publish_frontier(p);
 }
 
 }  // namespace
@@ -287,39 +548,49 @@ __global__ void __launch_bounds__(1024) sssp_init(SsspParams p) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += G) {
     p.dist[v] = v == p.source ? 0u : kInf;
     p.stamp[v] = kInf;
+    if (p.fmark) p.fmark[v] = kInf;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    p.fcur[0] = make_int2(p.source, 0);
-    p.hdr->aux[0] = 1ull;
+    p.fcur[0] = make_int4(p.source, 0, __ldg(p.off + p.source), __ldg(p.off + p.source + 1));
+    WsHeader *h = p.hdr;
+    h->aux[0] = 1ull;
+    h->nf_split = p.delta ? p.delta : kNoSplit;
+    h->nf_sub = p.sub_delta ? p.sub_delta : kNoSplit;
+    h->nf_split_old = 0u;
+    h->nf_dmin = kInf;
+    h->nf_hmin = kInf;
   }
 }
 
-// Consolidated child: warps take (vertex, edge chunk) units round-robin, or -
-// when the child is the only one of its round (grid level) - four at a time
-// from a shared cursor, so that no warp is left with a long tail of work. New
-// frontier vertices are staged per warp (see relax_edges_staged).
+// Consolidated child: warps take units round-robin, or - when the child is the
+// only one of its round (grid level) - one to four at a time from a shared
+// cursor, so that no warp is left with a long tail of work. New frontier
+// vertices are staged per warp (see relax_edges_staged).
 __global__ void __launch_bounds__(1024) sssp_child(SsspParams p, const int4 *__restrict__ units, int nunits,
                                                   unsigned r, unsigned long long *cursor, unsigned *heap_block) {
   extern __shared__ int s_stage[];  // per warp: kStage entries, then the count (stage_bytes)
   const int wib = threadIdx.x >> 5;
   WarpStage ws{s_stage + wib * (kStage + 1), s_stage + wib * (kStage + 1) + kStage};
   if (lane_id() == 0) *ws.cnt = 0;
-  __syncwarp();
-  auto unit = [&](int4 u) {
-    if (u.x < 0) return;
-    const int a0 = __ldg(p.off + u.x), b0 = __ldg(p.off + u.x + 1);
-    const int a = a0 + u.y * p.chunk;
-    relax_edges_staged(p, a, min(b0, a + p.chunk), (unsigned)u.z, r, ws);
-  };
+  phase_sync(p);
+  const unsigned S = s_ph.S;
+  auto unit = [&](int4 u) { relax_edges_staged(p, u.x, u.y, (unsigned)u.z, r, S, ws); };
   if (cursor) {
-    const unsigned long long grab = units_per_grab(nunits, (gridDim.x * blockDim.x) >> 5);
-    for (;;) {
-      unsigned long long i0 = 0;
-      if (lane_id() == 0) i0 = atomicAdd(cursor, grab);
-      i0 = __shfl_sync(0xffffffffu, i0, 0);
-      if (i0 >= (unsigned long long)nunits) break;
-      const int i1 = (int)min(i0 + grab, (unsigned long long)nunits);
-      for (int u = (int)i0; u < i1; ++u) unit(units[u]);
+    // every warp's first unit is its own (no atomic while units are fewer than
+    // warps); the rest come from the shared cursor
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    if (gw < nunits) unit(units[gw]);
+    if (nunits > nw) {
+      const unsigned long long grab = units_per_grab(nunits - nw, nw);
+      for (;;) {
+        unsigned long long i0 = 0;
+        if (lane_id() == 0) i0 = atomicAdd(cursor, grab) + (unsigned long long)nw;
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if (i0 >= (unsigned long long)nunits) break;
+        const int i1 = (int)min(i0 + grab, (unsigned long long)nunits);
+        for (int u = (int)i0; u < i1; ++u) unit(units[u]);
+      }
     }
   } else {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -332,10 +603,10 @@ __global__ void __launch_bounds__(1024) sssp_child(SsspParams p, const int4 *__r
 }
 
 // Basic-DP child (Fig. 1b's process_neighbors): thread per edge of one vertex.
-__global__ void __launch_bounds__(1024) sssp_vertex_child(SsspParams p, int u, unsigned du, unsigned r) {
-  const int a = __ldg(p.off + u), b = __ldg(p.off + u + 1);
+__global__ void __launch_bounds__(1024) sssp_vertex_child(SsspParams p, int a, int b, unsigned du, unsigned r) {
+  phase_sync(p);
   const int e = a + blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < b) relax(p, edge_col(p, e), du, edge_w(p, e), r);
+  if (e < b) relax(p, edge_col(p, e), du, edge_w(p, e), r, s_ph.S);
 }
 
 __device__ __forceinline__ void round_prologue(const SsspParams &p, unsigned r) {
@@ -369,18 +640,25 @@ __device__ __forceinline__ void round_stats(const SsspParams &p, unsigned long l
 template <int LEVEL>
 __global__ void __launch_bounds__(1024) sssp_parent_simple(SsspParams p, unsigned r) {
   round_prologue(p, r);
-  const int nf = frontier_size(p);
+  phase_sync(p);
+  const int nf = (int)s_ph.nf;
+  const unsigned s = s_ph.s;
+  const unsigned S = s_ph.S;
   const int G = gridDim.x * blockDim.x;
   unsigned long long relaxed = 0, inl = 0, buf = 0, launched = 0, failed = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += G) {
-    const int2 f = p.fcur[i];
-    const int a = __ldg(p.off + f.x), b = __ldg(p.off + f.x + 1);
+    const int4 f = p.fcur[i];
+    if (!relaxed_now(p, f, s)) {  // a heavy vertex above the sub-split waits for a later round
+      push_next(p, f.x, r);
+      continue;
+    }
+    const int a = f.z, b = f.w;
     relaxed += b - a;
     if (LEVEL == DPC_BASIC_DP && b - a > p.threshold) {
       buf++;
       if (take_launch_slot(&p.hdr->launches, p.launch_budget)) {
         sssp_vertex_child<<<ceil_div(b - a, p.child_threads), p.child_threads, 0, cudaStreamFireAndForget>>>(
-            p, f.x, (unsigned)f.y, r);
+            p, a, b, (unsigned)f.y, r);
         if (cudaGetLastError() == cudaSuccess) {
           launched++;
           continue;
@@ -390,7 +668,7 @@ __global__ void __launch_bounds__(1024) sssp_parent_simple(SsspParams p, unsigne
     } else {
       inl++;
     }
-    relax_all(p, a, b, (unsigned)f.y, r);
+    relax_all(p, a, b, (unsigned)f.y, r, S);
   }
   round_stats(p, relaxed, inl, buf, launched, failed);
 }
@@ -408,16 +686,19 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
   if (lane_id() == 0) *ws.cnt = 0;
   __syncwarp();
   round_prologue(p, r);
-  const int nf = frontier_size(p);
+  phase_sync(p);
+  const int nf = (int)s_ph.nf;
+  const unsigned sub = s_ph.s;
+  const unsigned S = s_ph.S;
   const int lane = lane_id();
   const int G = gridDim.x * blockDim.x;
   const int bstart = blockIdx.x * blockDim.x;
 
   int mine = 0;
   for (int i = bstart + threadIdx.x; i < nf; i += G) {
-    const int u = p.fcur[i].x;
-    const int deg = __ldg(p.off + u + 1) - __ldg(p.off + u);
-    if (deg > p.threshold) mine += ceil_div(deg, p.chunk);
+    const int4 f = p.fcur[i];
+    const int deg = f.w - f.z;
+    if (deg > p.threshold && relaxed_now(p, f, sub)) mine += ceil_div(deg, p.chunk);
   }
   // The group's buffer: a slice of the workspace pool, or (p.heap, warp and
   // block levels) a block of its own from the device heap, the paper's
@@ -447,7 +728,7 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
     if (!heap && base + gtotal > p.max_units) {  // only reachable with malformed input
       if (threadIdx.x == 0) sssp_fail(p, DPC_ERR_OVERFLOW);
       for (int j = base + threadIdx.x; j < min(base + gtotal, p.max_units); j += blockDim.x)
-        p.units[j] = make_int4(-1, 0, 0, 0);
+        p.units[j] = make_int4(0, 0, 0, -1);
       gtotal = 0;
     }
   } else {
@@ -470,7 +751,7 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
       if (!hblk) gtotal = 0;
     } else if (base + gtotal > p.max_units) {  // only reachable with malformed input
       if (lane == 0) sssp_fail(p, DPC_ERR_OVERFLOW);
-      for (int j = base + lane; j < min(base + gtotal, p.max_units); j += kWarp) p.units[j] = make_int4(-1, 0, 0, 0);
+      for (int j = base + lane; j < min(base + gtotal, p.max_units); j += kWarp) p.units[j] = make_int4(0, 0, 0, -1);
       gtotal = 0;
     }
   }
@@ -481,13 +762,19 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
   for (int i0 = bstart; i0 < nf; i0 += G) {
     const int i = i0 + threadIdx.x;
     int nu = 0, a = 0, b = 0;
-    int2 f = make_int2(0, 0);
+    int4 f = make_int4(0, 0, 0, 0);
+    bool work = false;
     if (i < nf) {
       f = p.fcur[i];
-      a = __ldg(p.off + f.x);
-      b = __ldg(p.off + f.x + 1);
-      relaxed += b - a;
-      if (gtotal && b - a > p.threshold) nu = ceil_div(b - a, p.chunk);
+      if (relaxed_now(p, f, sub)) {
+        work = true;
+        a = f.z;
+        b = f.w;
+        relaxed += b - a;
+        if (gtotal && b - a > p.threshold) nu = ceil_div(b - a, p.chunk);
+      } else {
+        push_next(p, f.x, r);  // a heavy vertex above the sub-split waits for a later round
+      }
     }
     int excl, step;
     if (LEVEL == DPC_BLOCK) {
@@ -499,12 +786,15 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
     }
     if (nu) {
       const int pos = run + excl;
-      for (int k = 0; k < nu; ++k) ubuf[pos + k] = make_int4(f.x, k, f.y, 0);
+      for (int k = 0; k < nu; ++k) {
+        const int ua = a + k * p.chunk;
+        ubuf[pos + k] = make_int4(ua, min(b, ua + p.chunk), f.y, f.x);
+      }
       buf++;
-    } else if (i < nf) {
+    } else if (work) {
       inl++;
     }
-    relax_inline_staged(p, a, b, (unsigned)f.y, r, i < nf && nu == 0, ws);
+    relax_inline_warp(p, a, b, (unsigned)f.y, r, S, work && nu == 0, ws);
     run += step;
   }
   stage_flush(p, ws);
@@ -527,7 +817,7 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
       }
       fl = __shfl_sync(0xffffffffu, fl, 0);
       if (fl) {
-        sssp_units_by_group(p, ubuf, base, base + gtotal, 0, 1, r);
+        sssp_units_by_group(p, ubuf, base, base + gtotal, 0, 1, r, S);
         __syncwarp();
         if (lane == 0 && hblk) free(hblk);
       }
@@ -549,7 +839,7 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
       }
       __syncthreads();
       if (s_fail) {
-        sssp_units_by_group(p, ubuf, base, base + gtotal, threadIdx.x >> 5, blockDim.x >> 5, r);
+        sssp_units_by_group(p, ubuf, base, base + gtotal, threadIdx.x >> 5, blockDim.x >> 5, r, S);
         __syncthreads();
         if (threadIdx.x == 0 && hblk) free(hblk);
       }
@@ -574,7 +864,7 @@ __global__ void __launch_bounds__(1024) sssp_parent(SsspParams p, unsigned r) {
         }
       }
       __syncthreads();
-      if (s_fail) sssp_units_by_group(p, p.units, 0, s_base, threadIdx.x >> 5, blockDim.x >> 5, r);
+      if (s_fail) sssp_units_by_group(p, p.units, 0, s_base, threadIdx.x >> 5, blockDim.x >> 5, r, S);
     }
   }
   round_stats(p, relaxed, inl, buf, launched, failed);
@@ -593,34 +883,91 @@ __device__ void launch_parent(const SsspParams &p, unsigned r, int nf, cudaStrea
   }
 }
 
-// After round r: freeze (vertex, distance) of the next frontier, reset the
-// round's buffers, and continue with round r+1 while the frontier is not empty.
+__global__ void sssp_split_min(SsspParams p, unsigned r);
+__global__ void sssp_split_apply(SsspParams p, unsigned r);
+
+// What follows round r (or a split before round r+1), decided by one thread
+// once the frontier for the next round is published: its parent, the split,
+// or the end of the call. Device-launched levels only.
+__device__ void continue_after(const SsspParams &p, unsigned next_round) {
+  WsHeader *h = p.hdr;
+  const unsigned long long nn = ld_volatile(&h->aux[0]);
+  const unsigned long long nfar = ld_volatile(&h->nf_far[ld_volatile(&h->nf_cur)]);
+  h->round = next_round;
+  __threadfence();
+  const bool ok = ld_volatile(&h->status) == 0u;
+  if (ok && nn > 0 && next_round < p.max_rounds) {
+    launch_parent(p, next_round, (int)nn, cudaStreamTailLaunch);
+  } else if (ok && nn == 0 && nfar > 0) {
+    const int blocks = (int)min((nfar + 255) / 256, (unsigned long long)p.commit_blocks);
+    sssp_split_min<<<blocks > 0 ? blocks : 1, 256, 0, cudaStreamTailLaunch>>>(p, next_round);
+  } else {
+    if (ok && nn > 0) sssp_fail(p, DPC_ERR_OVERFLOW);  // the round cap was reached with work left
+    if (p.stats) p.stats->rounds = next_round;
+    return;
+  }
+  if (cudaGetLastError() != cudaSuccess) sssp_fail(p, DPC_ERR_DEVICE);
+  else stat_add(p.stats, &dpc_stats::aux_launches, 1);
+}
+
+// After round r: the vertices that dropped (and heavy ones that wait) become
+// the next frontier or go to the far pile.
 __global__ void __launch_bounds__(256) sssp_commit(SsspParams p, unsigned r) {
-  const int nn = (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor2);
+  phase_sync(p);
+  const int nn = (int)s_ph.next;
+  const Split q = read_split();
   const int G = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += G) {
-    const int v = __ldcg(p.fnext + i);
-    p.fcur[i] = make_int2(v, (int)__ldcg(p.dist + v));
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i0 = gtid - (int)lane_id(); i0 < nn; i0 += G) {
+    const int i = i0 + (int)lane_id();
+    commit_vertex(p, i < nn, i < nn ? __ldcg(p.fnext + i) : 0, q);
   }
   if (!last_block_done(&p.hdr->done_blocks2)) return;
   if (threadIdx.x == 0) {
-    p.hdr->aux[0] = (unsigned long long)nn;
-    p.hdr->cursor2 = 0ull;
-    p.hdr->cursor = 0ull;
-    p.hdr->aux[2] = 0ull;    // the grid-level child's unit cursor
-    p.hdr->launches = 0ull;  // the round's children have all finished: their pool slots are free
-    p.hdr->round = r + 1;
-    __threadfence();
-    const bool more = nn > 0 && r + 1 <= (unsigned)p.n && p.hdr->status == 0u;
-    if (p.level != DPC_FLAT) {
-      if (more) {
-        launch_parent(p, r + 1, nn, cudaStreamTailLaunch);
-        if (cudaGetLastError() != cudaSuccess) sssp_fail(p, DPC_ERR_DEVICE);
-        else stat_add(p.stats, &dpc_stats::aux_launches, 1);
-      } else if (p.stats) {
-        p.stats->rounds = r + 1;
-      }
+    publish_frontier(p);
+    if (p.level != DPC_FLAT) continue_after(p, r + 1);
+  }
+}
+
+// The split, first pass (grid-stride over the current far list).
+__global__ void __launch_bounds__(256) sssp_split_min(SsspParams p, unsigned r) {
+  phase_sync(p);
+  const Split q = read_split();
+  const int nfar = (int)s_ph.nfar;
+  const int G = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x - (int)lane_id(); i0 < nfar; i0 += G) {
+    const int i = i0 + (int)lane_id();
+    split_min_vertex(p, i < nfar, i < nfar ? __ldcg(p.far[q.cur] + i) : 0, q);
+  }
+  if (!last_block_done(&p.hdr->done_blocks2)) return;
+  if (threadIdx.x == 0) {
+    const bool live = advance_split(p);
+    if (p.level == DPC_FLAT) return;
+    if (!live) {
+      if (p.stats) p.stats->rounds = r;
+      return;
     }
+    sssp_split_apply<<<gridDim.x, 256, 0, cudaStreamTailLaunch>>>(p, r);
+    if (cudaGetLastError() != cudaSuccess) sssp_fail(p, DPC_ERR_DEVICE);
+    else stat_add(p.stats, &dpc_stats::aux_launches, 1);
+  }
+}
+
+// The split, second pass.
+__global__ void __launch_bounds__(256) sssp_split_apply(SsspParams p, unsigned r) {
+  phase_sync(p);
+  const Split q = read_split();
+  const unsigned epoch = s_ph.epoch;
+  const int nfar = (int)s_ph.nfar;
+  const int G = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x - (int)lane_id(); i0 < nfar; i0 += G) {
+    const int i = i0 + (int)lane_id();
+    split_apply_vertex(p, i < nfar, i < nfar ? __ldcg(p.far[q.cur] + i) : 0, q, epoch);
+  }
+  if (!last_block_done(&p.hdr->done_blocks2)) return;
+  if (threadIdx.x == 0) {
+    finish_split(p);
+    if (p.level != DPC_FLAT) continue_after(p, r);
   }
 }
 
@@ -629,19 +976,19 @@ __global__ void __launch_bounds__(256) sssp_commit(SsspParams p, unsigned r) {
 // The grid level's rounds inside one cooperative grid: per round a parent
 // phase (large frontier vertices' units into the buffer, short ones relaxed
 // inline), the consolidated child's loop over the buffer, and the commit, each
-// separated by a grid barrier instead of a device launch. The rounds keep the
-// Jacobi semantics of the other levels (the commit snapshots distances after
-// every relaxation of the round), so frontiers, rounds and relaxation counts
-// are those of the grid level.
+// separated by a grid barrier instead of a device launch; a split is two more
+// phases. The rounds keep the Jacobi semantics of the other levels (the commit
+// snapshots distances after every relaxation of the round), so frontiers,
+// rounds and relaxation counts are those of the grid level.
 namespace {
 
-
-enum : int { kBarPlain = 0, kBarChildren = 1, kBarRound = 2 };
+enum : int { kBarPlain = 0, kBarChildren = 1, kBarRound = 2, kBarSplitMin = 3, kBarSplitApply = 4 };
 
 // Multi-use barrier (arrivals only grow; the k-th barrier is complete at k *
 // gridDim.x arrivals). The last block to arrive acts before it releases the
-// others: after the children it publishes the next frontier's size; after the
-// commit it makes that the current size and resets the round's counters.
+// others: after the children it publishes the list of vertices that dropped;
+// after the commit it publishes the next frontier; after a split's passes it
+// sets the new split or makes the far vertices below it the frontier.
 // Bounded wait; false (with DPC_ERR_TIMEOUT) when it runs out.
 __device__ bool queue_barrier(const SsspParams &p, unsigned k, int kind) {
   __shared__ int s_ok;
@@ -651,12 +998,13 @@ __device__ bool queue_barrier(const SsspParams &p, unsigned k, int kind) {
     int ok = 1;
     if (atomicAdd(&p.hdr->done_blocks2, 1u) == k * gridDim.x - 1) {
       if (kind == kBarChildren) {
-        p.hdr->aux[1] = *reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor2);
+        p.hdr->aux[1] = ld_volatile(&p.hdr->cursor2);
       } else if (kind == kBarRound) {
-        p.hdr->aux[0] = p.hdr->aux[1];
-        p.hdr->cursor2 = 0ull;
-        p.hdr->cursor = 0ull;
-        p.hdr->aux[2] = 0ull;
+        publish_frontier(p);
+      } else if (kind == kBarSplitMin) {
+        advance_split(p);
+      } else if (kind == kBarSplitApply) {
+        finish_split(p);
       }
       __threadfence();
       atomicExch(&p.hdr->round, k);
@@ -672,6 +1020,7 @@ __device__ bool queue_barrier(const SsspParams &p, unsigned k, int kind) {
       }
     }
     __threadfence();
+    if (ok) phase_load(p);  // the next phase's state, once per block
     s_ok = ok;
   }
   __syncthreads();
@@ -686,26 +1035,54 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
   extern __shared__ int s_stage[];  // per warp: kStage entries, then the count (stage_bytes)
   const WarpStage ws{s_stage + (threadIdx.x >> 5) * (kStage + 1), s_stage + (threadIdx.x >> 5) * (kStage + 1) + kStage};
   if (lane_id() == 0) *ws.cnt = 0;
-  __syncwarp();
+  phase_sync(p);
   const int lane = lane_id();
   const int G = gridDim.x * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long relaxed = 0, inl = 0, buf = 0;
   unsigned k = 0, r = 0;
-  for (; r <= (unsigned)p.n; ++r) {
-    const int nf = frontier_size(p);
-    if (nf == 0) break;
+  for (;;) {
+    const int nf = (int)s_ph.nf;
+    if (nf == 0) {
+      // the split: the far pile's smallest live distance, then the new frontier from it
+      const Split q0 = read_split();
+      const int nfar = (int)s_ph.nfar;
+      if (nfar == 0) break;
+      for (int i0 = gtid - lane; i0 < nfar; i0 += G)
+        split_min_vertex(p, i0 + lane < nfar, i0 + lane < nfar ? __ldcg(p.far[q0.cur] + i0 + lane) : 0, q0);
+      if (!queue_barrier(p, ++k, kBarSplitMin)) return;
+      const Split q = read_split();
+      if (s_ph.nfar == 0ull) break;  // every far vertex was stale
+      const unsigned epoch = s_ph.epoch;
+      for (int i0 = gtid - lane; i0 < nfar; i0 += G)
+        split_apply_vertex(p, i0 + lane < nfar, i0 + lane < nfar ? __ldcg(p.far[q.cur] + i0 + lane) : 0, q,
+                           epoch);
+      if (!queue_barrier(p, ++k, kBarSplitApply)) return;
+      continue;
+    }
+    if (r >= p.max_rounds) {
+      if (gtid == 0) sssp_fail(p, DPC_ERR_OVERFLOW);  // the round cap was reached with work left
+      break;
+    }
+    const unsigned sub = s_ph.s;
+    const unsigned S = s_ph.S;
     // parent phase: units of the large frontier vertices (one reservation per warp), short ones inline
     for (int i0 = gtid - lane; i0 < nf; i0 += G) {
       const int i = i0 + lane;
       int nu = 0, a = 0, b = 0;
-      int2 f = make_int2(0, 0);
+      int4 f = make_int4(0, 0, 0, 0);
+      bool work = false;
       if (i < nf) {
-        f = p.fcur[i];
-        a = __ldg(p.off + f.x);
-        b = __ldg(p.off + f.x + 1);
-        relaxed += b - a;
-        if (b - a > p.threshold) nu = ceil_div(b - a, p.chunk);
+        f = __ldcg(p.fcur + i);
+        if (relaxed_now(p, f, sub)) {
+          work = true;
+          a = f.z;
+          b = f.w;
+          relaxed += b - a;
+          if (b - a > p.threshold) nu = ceil_div(b - a, p.chunk);
+        } else {
+          push_next(p, f.x, r);  // a heavy vertex above the sub-split waits for a later round
+        }
       }
       const int inc = warp_inclusive_scan(nu);
       const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
@@ -718,40 +1095,47 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
       }
       if (nu) {
         const int pos = (int)base + inc - nu;
-        for (int q = 0; q < nu; ++q) p.units[pos + q] = make_int4(f.x, q, f.y, 0);
+        for (int q = 0; q < nu; ++q) {
+          const int ua = a + q * p.chunk;
+          p.units[pos + q] = make_int4(ua, min(b, ua + p.chunk), f.y, f.x);
+        }
         buf++;
-      } else if (i < nf) {
+      } else if (work) {
         inl++;
       }
-      relax_inline_staged(p, a, b, (unsigned)f.y, r, i < nf && nu == 0, ws);
+      relax_inline_warp(p, a, b, (unsigned)f.y, r, S, work && nu == 0, ws);
     }
     if (!queue_barrier(p, ++k, kBarPlain)) return;
-    // the consolidated child's loop, units taken from a shared cursor
-    const int total = (int)min(*reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor),
-                               (unsigned long long)p.max_units);
-    const unsigned long long grab = units_per_grab(total, G >> 5);
-    for (;;) {
-      unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(&p.hdr->aux[2], grab);
-      i0 = __shfl_sync(0xffffffffu, i0, 0);
-      if (i0 >= (unsigned long long)total) break;
-      const int i1 = (int)min(i0 + grab, (unsigned long long)total);
-      for (int u = (int)i0; u < i1; ++u) {
-        const int4 un = __ldcg(p.units + u);
-        if (un.x < 0) continue;
-        const int a0 = __ldg(p.off + un.x), b0 = __ldg(p.off + un.x + 1);
-        const int a = a0 + un.y * p.chunk;
-        relax_edges_staged(p, a, min(b0, a + p.chunk), (unsigned)un.z, r, ws);
+    // the consolidated child's loop: every warp's first unit is its own (no
+    // atomic while units are fewer than warps), the rest come from a shared cursor
+    const int total = (int)min(s_ph.units, (unsigned long long)p.max_units);
+    const int nw = G >> 5;
+    if ((gtid >> 5) < total) {
+      const int4 un = __ldcg(p.units + (gtid >> 5));
+      relax_edges_staged(p, un.x, un.y, (unsigned)un.z, r, S, ws);
+    }
+    if (total > nw) {
+      const unsigned long long grab = units_per_grab(total - nw, nw);
+      for (;;) {
+        unsigned long long i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&p.hdr->aux[2], grab) + (unsigned long long)nw;
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        if (i0 >= (unsigned long long)total) break;
+        const int i1 = (int)min(i0 + grab, (unsigned long long)total);
+        for (int u = (int)i0; u < i1; ++u) {
+          const int4 un = __ldcg(p.units + u);
+          relax_edges_staged(p, un.x, un.y, (unsigned)un.z, r, S, ws);
+        }
       }
     }
     stage_flush(p, ws);
     if (!queue_barrier(p, ++k, kBarChildren)) return;
-    // commit: freeze (vertex, distance) of the next frontier
-    const int nn = (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->aux[1]);
-    for (int i = gtid; i < nn; i += G) {
-      const int v = __ldcg(p.fnext + i);
-      p.fcur[i] = make_int2(v, (int)__ldcg(p.dist + v));
-    }
+    // commit: the next frontier's entries and the far pile
+    const int nn = (int)s_ph.aux1;
+    const Split q = read_split();
+    for (int i0 = gtid - lane; i0 < nn; i0 += G)
+      commit_vertex(p, i0 + lane < nn, i0 + lane < nn ? __ldcg(p.fnext + i0 + lane) : 0, q);
+    ++r;
     if (!queue_barrier(p, ++k, kBarRound)) return;
   }
   round_stats(p, relaxed, inl, buf, 0, 0);
@@ -783,12 +1167,42 @@ size_t sssp_max_units(int n, int m, int threshold, int chunk) {
 
 size_t sssp_workspace_bytes(int n, int m, dpc_level level, const LaunchCfg &c) {
   size_t b = kHeaderBytes;
-  b += align_up((size_t)n * sizeof(int2), 256);
-  b += align_up((size_t)n * sizeof(int), 256);
-  b += align_up((size_t)n * sizeof(unsigned), 256);
+  b += align_up((size_t)n * sizeof(int4), 256);      // fcur
+  b += align_up((size_t)n * sizeof(int), 256);       // fnext
+  b += align_up((size_t)n * sizeof(unsigned), 256);  // stamp
+  if (c.delta) b += 2 * align_up((size_t)n * sizeof(int), 256) + align_up((size_t)n * sizeof(unsigned), 256);
   if (level == DPC_WARP || level == DPC_BLOCK || level == DPC_GRID || level == DPC_QUEUE)
     b += align_up(sssp_max_units(n, m, c.threshold, c.chunk) * sizeof(int4), 256);
   return b;
+}
+
+void sssp_carve(SsspParams &p, void *workspace, int n, int m, dpc_level level, const LaunchCfg &c) {
+  char *b = static_cast<char *>(workspace);
+  p.hdr = reinterpret_cast<WsHeader *>(b);
+  b += kHeaderBytes;
+  p.fcur = reinterpret_cast<int4 *>(b);
+  b += align_up((size_t)n * sizeof(int4), 256);
+  p.fnext = reinterpret_cast<int *>(b);
+  b += align_up((size_t)n * sizeof(int), 256);
+  p.stamp = reinterpret_cast<unsigned *>(b);
+  b += align_up((size_t)n * sizeof(unsigned), 256);
+  p.far[0] = p.far[1] = nullptr;
+  p.fmark = nullptr;
+  if (c.delta) {
+    p.far[0] = reinterpret_cast<int *>(b);
+    b += align_up((size_t)n * sizeof(int), 256);
+    p.far[1] = reinterpret_cast<int *>(b);
+    b += align_up((size_t)n * sizeof(int), 256);
+    p.fmark = reinterpret_cast<unsigned *>(b);
+    b += align_up((size_t)n * sizeof(unsigned), 256);
+  }
+  p.units = nullptr;
+  p.max_units = 0;
+  if (level == DPC_WARP || level == DPC_BLOCK || level == DPC_GRID || level == DPC_QUEUE) {
+    const size_t mu = sssp_max_units(n, m, c.threshold, c.chunk);
+    p.units = reinterpret_cast<int4 *>(b);
+    p.max_units = (int)(mu > (size_t)0x7FFFFFFF ? 0x7FFFFFFF : mu);
+  }
 }
 
 const void *sssp_parent_kernel(dpc_level level) {
@@ -823,18 +1237,36 @@ cudaError_t sssp_launch(SsspParams &p, dpc_level level, cudaStream_t s, unsigned
     }
     return cudaGetLastError();
   }
-  // flat: host-driven rounds (no device launches at all)
-  unsigned long long &nf = host_scratch().count;
-  nf = 1;
+  // flat: host-driven rounds and splits (no device launches at all); after
+  // every step the frontier size and the far pile's size come back
+  HostScratch &hs = host_scratch();
   unsigned r = 0;
-  for (; nf > 0 && r <= (unsigned)p.n; ++r) {
-    const int need = ceil_div((int)nf, p.parent_threads);
-    const int blocks = need < p.parent_blocks ? need : p.parent_blocks;
-    sssp_parent_simple<DPC_FLAT><<<blocks, p.parent_threads, 0, s>>>(p, r);
-    sssp_commit<<<p.commit_blocks, 256, 0, s>>>(p, r);
+  unsigned long long nf = 1;
+  for (;;) {
+    if (nf > 0) {
+      if (r >= p.max_rounds) break;
+      const int need = ceil_div((int)nf, p.parent_threads);
+      const int blocks = need < p.parent_blocks ? need : p.parent_blocks;
+      sssp_parent_simple<DPC_FLAT><<<blocks, p.parent_threads, 0, s>>>(p, r);
+      sssp_commit<<<p.commit_blocks, 256, 0, s>>>(p, r);
+      ++r;
+    } else {
+      sssp_split_min<<<p.commit_blocks, 256, 0, s>>>(p, r);
+      sssp_split_apply<<<p.commit_blocks, 256, 0, s>>>(p, r);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(&nf, &p.hdr->aux[0], sizeof(nf), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(hs.sizes, &p.hdr->aux[0], sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(hs.sizes + 1, p.hdr->nf_far, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             s)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(&hs.value, &p.hdr->nf_cur, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    nf = hs.sizes[0];
+    const unsigned long long nfar = hs.sizes[1 + (hs.value & 1)];
+    if (nf == 0 && nfar == 0) break;
   }
   if (rounds_out) *rounds_out = r;
   return cudaSuccess;

@@ -46,7 +46,8 @@ class Tuning(ctypes.Structure):
 
     _fields_ = [("threshold", ctypes.c_int32), ("parent_blocks", ctypes.c_int32), ("parent_threads", ctypes.c_int32),
                 ("child_blocks", ctypes.c_int32), ("child_threads", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("kc", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("kc", ctypes.c_int32), ("flags", ctypes.c_uint32), ("delta", ctypes.c_int32),
+                ("sub_delta", ctypes.c_int32)]
 
 
 class Job(ctypes.Structure):

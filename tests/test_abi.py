@@ -95,7 +95,7 @@ def test_host_only_calls(lib):
     lib.dpc_status_string.restype = ctypes.c_char_p
     assert lib.dpc_status_string(0) == b"DPC_OK"
     assert b"WORKSPACE" in lib.dpc_status_string(2)
-    assert lib.dpc_abi_version() == 1
+    assert lib.dpc_abi_version() == 2
     out = ctypes.c_size_t(0)
     # workspace queries are pure host arithmetic
     for level in range(5):

@@ -1,9 +1,11 @@
 """Do the oracle's pins catch plausible mistakes? Each case rebuilds
 dpc_oracle.c with one slip planted (a dropped term, a comparison off by one, a
 Gauss-Seidel read where the round is Jacobi, a wrong modulus, a LIFO where the
-search is FIFO), binds the broken copy in place of the real oracle and runs
-the CPU pins of the function it touches: at least one pin must fail. The
-unmodified oracle passes every one of them (the regular CPU tests)."""
+search is FIFO, a split that is not aligned to its bucket), binds the broken
+copy in place of the real oracle and runs the CPU pins of the function it
+touches: at least one pin must fail. The unmodified oracle passes every one of
+them (the regular CPU tests). Every planted slip keeps the oracle's memory
+accesses in bounds, so a broken copy fails a pin instead of the process."""
 import inspect
 import os
 import subprocess
@@ -28,9 +30,27 @@ MUTANTS = {
                                   [test_oracle_tree]),
     # SSSP
     "dijkstra_max_heap": ("if (h[p].d <= h[i].d) break;", "if (h[p].d >= h[i].d) break;", [test_oracle_sssp]),
-    "frontier_reads_live_distance": ("uint64_t nd = dprev[u] + (uint64_t)w[e];",
-                                     "uint64_t nd = d[u] + (uint64_t)w[e];", [test_oracle_sssp]),
-    "frontier_heavy_at_threshold": ("> threshold) hv++;", ">= threshold) hv++;", [test_oracle_sssp]),
+    "frontier_reads_live_distance": ("int32_t u = F[i];\n      for (int64_t e = off[u]; e < off[u + 1]; ++e) {\n"
+                                     "        int32_t v = col[e];\n        uint64_t nd = dprev[u] + (uint64_t)w[e];",
+                                     "int32_t u = F[i];\n      for (int64_t e = off[u]; e < off[u + 1]; ++e) {\n"
+                                     "        int32_t v = col[e];\n        uint64_t nd = d[u] + (uint64_t)w[e];",
+                                     [test_oracle_sssp]),
+    "nearfar_reads_live_distance": ("int32_t u = act[i];\n      for (int64_t e = off[u]; e < off[u + 1]; ++e) {\n"
+                                    "        int32_t v = col[e];\n        uint64_t nd = dprev[u] + (uint64_t)w[e];",
+                                    "int32_t u = act[i];\n      for (int64_t e = off[u]; e < off[u + 1]; ++e) {\n"
+                                    "        int32_t v = col[e];\n        uint64_t nd = d[u] + (uint64_t)w[e];",
+                                    [test_oracle_sssp]),
+    "frontier_heavy_at_threshold": ("off[F[i] + 1] - off[F[i]] > threshold) hv++;",
+                                    "off[F[i] + 1] - off[F[i]] >= threshold) hv++;", [test_oracle_sssp]),
+    # the near-far split and the sub-split
+    "nearfar_live_far_vertex_dropped": ("if (d[v] < S_old) { in_far[v] = 0; continue; }",
+                                        "if (d[v] <= S_old) { in_far[v] = 0; continue; }", [test_oracle_sssp]),
+    "nearfar_split_not_bucket_aligned": ("S = (dmin / delta + 1) * (uint64_t)delta;", "S = dmin + delta;",
+                                         [test_oracle_sssp]),
+    "subsplit_light_bound": ("if (off[v + 1] - off[v] <= threshold || d[v] < s) act[na++] = v;",
+                             "if (off[v + 1] - off[v] < threshold || d[v] < s) act[na++] = v;", [test_oracle_sssp]),
+    "subsplit_not_bucket_aligned": ("s = (hmin / sub_delta + 1) * (uint64_t)sub_delta;", "s = hmin + sub_delta;",
+                                    [test_oracle_sssp]),
     # SpMV
     "spmv_signed_row_scale": ("a += p < 0 ? -p : p;", "a += p;", [test_oracle_spmv]),
     "spmv_single_precision_sum": ("double s = 0.0, a = 0.0;", "float s = 0.0f; double a = 0.0;",

@@ -75,6 +75,63 @@ def test_hand_worked_near_far():
         assert (r.relaxations, r.splits) == (want["relaxations"], want["splits"]), delta
 
 
+def test_hand_worked_sub_split():
+    d = json.load(open(os.path.join(GOLDEN, "sssp_hand.json")))
+    off, col, w = csr_from_edges(d["n"], d["edges"])
+    for want in d["subsplit"]:
+        r = oracle.sssp_nearfar(off, col, w, d["source"], want["delta"], d["threshold"], want["sub_delta"])
+        np.testing.assert_array_equal(r.dist, np.array(d["dist"], np.uint32))
+        assert r.frontier_size.tolist() == want["frontier_size"]
+        assert r.heavy.tolist() == want["heavy"]
+        assert (r.relaxations, r.splits, r.subsplits) == (want["relaxations"], want["splits"], want["subsplits"])
+
+
+@pytest.mark.parametrize("scale,seed", [(8, 1), (11, 2)])
+def test_sub_split_width_one_on_heavy_vertices_relaxes_each_once(scale, seed):
+    """Every vertex heavy (threshold -1), no split, sub-split width 1, weights
+    >= 1: a round relaxes exactly the vertices of the smallest pending
+    distance, which are final, so the rounds are the distinct distances in
+    increasing order and each sub-split advance opens the next one."""
+    g = gen.rmat(scale, seed=seed)
+    d = oracle.sssp_dijkstra(g.off, g.col, g.w, 0)
+    deg = np.diff(g.off)
+    reached = d != INF
+    values, counts = np.unique(d[reached], return_counts=True)
+    r = oracle.sssp_nearfar(g.off, g.col, g.w, 0, 0, -1, 1)
+    np.testing.assert_array_equal(r.dist, d)
+    assert r.frontier_size.tolist() == counts.tolist()
+    assert r.heavy.tolist() == counts.tolist()
+    assert r.relaxations == int(deg[reached].sum())
+    assert (r.splits, r.subsplits) == (0, r.rounds - 1)
+
+
+@pytest.mark.parametrize("scale,seed", [(10, 2), (12, 1)])
+def test_sub_split_without_heavy_vertices_changes_nothing(scale, seed):
+    """With a threshold above every out-degree no vertex is heavy: the runs with
+    and without the sub-split are the same."""
+    g = gen.rmat(scale, whi=1000, seed=seed)
+    top = int(np.diff(g.off).max())
+    for delta in (0, 60):
+        a = oracle.sssp_nearfar(g.off, g.col, g.w, 0, delta, top, 0)
+        b = oracle.sssp_nearfar(g.off, g.col, g.w, 0, delta, top, 7)
+        assert a.frontier_size.tolist() == b.frontier_size.tolist()
+        assert (a.relaxations, a.splits, b.subsplits) == (b.relaxations, b.splits, 0)
+
+
+def test_sub_split_path_closed_form():
+    # the path of test_near_far_path_closed_form with every vertex heavy: one vertex per round, and a
+    # sub-split advance each time the next vertex lies above the current sub-bucket
+    k = 40
+    off, col, w = csr_from_edges(k, [(i, i + 1, i + 1) for i in range(k - 1)])
+    want = np.array([j * (j + 1) // 2 for j in range(k)], np.uint32)
+    for sub in (1, 3, 10, 100):
+        r = oracle.sssp_nearfar(off, col, w, 0, 0, -1, sub)
+        np.testing.assert_array_equal(r.dist, want)
+        assert r.frontier_size.tolist() == [1] * k and r.relaxations == k - 1
+        buckets = [int(x) // sub for x in want]
+        assert r.subsplits == sum(1 for j in range(1, k) if buckets[j] != buckets[j - 1])
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_near_far_matches_floyd_warshall(seed):
     rng = np.random.default_rng(50 + seed)
@@ -83,8 +140,9 @@ def test_near_far_matches_floyd_warshall(seed):
                          seed=seed)
     fw = floyd_warshall(n, g.off, g.col, g.w)
     for s in range(0, n, 3):
-        for delta in (1, 7, 50, 1 << 30):
-            np.testing.assert_array_equal(oracle.sssp_nearfar(g.off, g.col, g.w, s, delta, 2).dist, as_u32(fw[s]))
+        for delta, sub in ((1, 0), (7, 0), (50, 3), (1 << 30, 0), (0, 2), (9, 1)):
+            np.testing.assert_array_equal(oracle.sssp_nearfar(g.off, g.col, g.w, s, delta, 2, sub).dist,
+                                          as_u32(fw[s]))
 
 
 @pytest.mark.parametrize("scale,seed", [(8, 1), (10, 2), (12, 1)])
