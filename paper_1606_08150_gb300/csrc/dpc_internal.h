@@ -44,15 +44,12 @@ struct WsHeader {
   alignas(128) unsigned long long nf_near;  // entries of the next frontier (the near set) written so far
   unsigned long long nf_elig;               // of those, the ones the next round relaxes
   unsigned nf_hmin;                         // smallest distance of a heavy near vertex that waits
-  // line 6: far-pile appends (during the relaxations)
-  alignas(128) unsigned long long nf_far[2];  // far pile sizes: the current list and the other
-  // line 7: the split (read by every phase, written between phases)
-  alignas(128) unsigned nf_split;             // split distance S (all ones: no split; finite distances are below it)
-  unsigned nf_sub;                            // sub-split distance s for heavy vertices (all ones: none)
-  unsigned nf_split_old;                      // S before the split in progress
-  unsigned nf_dmin;                           // smallest live far-pile distance (split in progress)
-  unsigned nf_epoch;                          // far-pile epoch: a vertex is in the pile when its mark equals it
-  unsigned nf_cur;                            // index of the current far list
+  // line 6: the split (read by every phase, written between phases)
+  alignas(128) unsigned nf_split;  // split distance S (all ones: no split; finite distances are below it)
+  unsigned nf_sub;                 // sub-split distance s for heavy vertices (all ones: none)
+  unsigned nf_split_old;           // S before the split in progress
+  unsigned nf_dmin;                // smallest distance at or above S (split in progress)
+  unsigned nf_done;                // 1: a split found no vertex at or above S (the run is over)
 };
 constexpr size_t kHeaderBytes = 1024;
 static_assert(sizeof(WsHeader) <= kHeaderBytes, "workspace header too large");
@@ -238,8 +235,6 @@ struct SsspParams {
                       // first edge, end edge)
   int *fnext;         // vertices whose distance dropped in the round, and heavy ones that wait
   unsigned *stamp;    // last round in which a vertex entered fnext
-  int *far[2];        // far piles (near-far split only)
-  unsigned *fmark;    // far-pile epoch of each vertex (near-far split only)
   int4 *units;        // (first edge, end edge, distance of the vertex, vertex)
   WsHeader *hdr;      // cursor: units; cursor2: |fnext|; aux[0]: |fcur|; nf_*: the split
   dpc_stats *stats;

@@ -10,9 +10,14 @@
 //
 // Optionally the rounds follow the near-far work split of Davidson, Baxter,
 // Garland & Owens (IPDPS 2014): a split distance S (a multiple of `delta`)
-// sends vertices that dropped to d >= S to a far pile instead of the next
-// frontier; when the frontier runs empty, S moves to the bucket above the
-// smallest live far distance and those far vertices form the next frontier.
+// keeps vertices that dropped to d >= S out of the next frontier (the far
+// pile); when the frontier runs empty, S moves to the bucket above the
+// smallest far distance and those far vertices form the next frontier. The
+// far pile is kept implicitly: a vertex is relaxed only while its distance is
+// below the current split, and the split only grows, so after a round the far
+// pile is exactly the set of vertices with a finite distance >= S, which a
+// split finds by scanning the distances (two coalesced passes) instead of
+// appending every far drop to a list.
 // A finer sub-split s (a multiple of `sub_delta`) holds heavy frontier
 // vertices (above the threshold) back while their distance is not below s, so
 // that a hub is relaxed once its distance has settled instead of on every
@@ -31,10 +36,10 @@
 //               distance, edge range), sends far vertices to the far pile, and
 //               its last block tail-launches parent(r+1), or - when the
 //               frontier is empty and the far pile is not - the split.
-//   split       split_min (smallest live far distance, the new S and s), then
-//               split_apply (far vertices below the new S become the
-//               frontier, the others move to the second far list), whose last
-//               block tail-launches parent(r+1).
+//   split       split_min (smallest distance >= S over all vertices, the new
+//               S and s), then split_apply (vertices with distance in [old S,
+//               new S) become the frontier), whose last block tail-launches
+//               parent(r+1).
 // The flat level runs the same kernels from a host loop, reading the frontier
 // and far-pile sizes back after every step; the queue level runs every phase
 // in one cooperative grid, separated by grid barriers.
@@ -72,12 +77,10 @@ struct Phase {
   unsigned long long aux1;   // queue level: entries of the round's list, published after the children
   unsigned long long next;   // entries of the round's list so far (cursor2)
   unsigned long long units;  // units in the buffer
-  unsigned long long nfar;   // entries of the current far list
   unsigned S;                // split distance: below it a vertex that dropped joins the next frontier
   unsigned s;                // sub-split: a heavy frontier vertex is relaxed below it
-  unsigned S_old;            // (split in progress) far vertices below it are stale
-  unsigned cur;              // current far list
-  unsigned epoch;            // far-pile epoch
+  unsigned S_old;            // (split in progress) the split before it
+  unsigned done;             // a split found no vertex at or above S
 };
 __shared__ Phase s_ph;
 
@@ -90,10 +93,7 @@ __device__ __forceinline__ void phase_load(const SsspParams &p) {
   s_ph.S = ld_volatile(&h->nf_split);
   s_ph.s = ld_volatile(&h->nf_sub);
   s_ph.S_old = ld_volatile(&h->nf_split_old);
-  s_ph.epoch = ld_volatile(&h->nf_epoch);
-  const unsigned cur = ld_volatile(&h->nf_cur);
-  s_ph.cur = cur;
-  s_ph.nfar = ld_volatile(&h->nf_far[cur]);
+  s_ph.done = ld_volatile(&h->nf_done);
 }
 
 // Every thread of the block; at the start of a device-launched kernel.
@@ -112,28 +112,6 @@ __device__ __forceinline__ void push_next(const SsspParams &p, int v, unsigned r
   p.fnext[base + g.thread_rank()] = v;
 }
 
-// v (whose distance dropped to S or more) joins the far pile once per epoch;
-// warp-aggregated append to the current far list.
-__device__ __forceinline__ void push_far(const SsspParams &p, int v) {
-  const unsigned epoch = s_ph.epoch;
-  if (atomicExch(p.fmark + v, epoch) == epoch) return;
-  const unsigned cur = s_ph.cur;
-  cg::coalesced_group g = cg::coalesced_threads();
-  unsigned long long base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(&p.hdr->nf_far[cur], (unsigned long long)g.size());
-  base = g.shfl(base, 0);
-  p.far[cur][base + g.thread_rank()] = v;
-}
-
-// Where a vertex whose distance dropped to d goes: the next frontier below the
-// split S (once per round), else the far pile. A vertex that drops first to
-// S or more and later in the same round below S is in both; its far entry is
-// stale and the split drops it (its distance is below the old split by then).
-__device__ __forceinline__ void push_dropped(const SsspParams &p, int v, unsigned d, unsigned r, unsigned S) {
-  if (d < S) push_next(p, v, r);
-  else push_far(p, v);
-}
-
 __device__ __forceinline__ void relax(const SsspParams &p, int v, unsigned du, unsigned w, unsigned r, unsigned S) {
   const unsigned long long nd = (unsigned long long)du + w;
   if (nd >= kInf) {
@@ -143,7 +121,7 @@ __device__ __forceinline__ void relax(const SsspParams &p, int v, unsigned du, u
   const unsigned d = (unsigned)nd;
   if (d < __ldcg(p.dist + v)) {
     atomicMin(p.dist + v, d);  // result unused: a reduction, no round trip (see relax_batch)
-    push_dropped(p, v, d, r, S);
+    if (d < S) push_next(p, v, r);  // at or above the split: the far pile, which needs no record
   }
 }
 
@@ -167,8 +145,8 @@ __device__ __forceinline__ unsigned edge_w(const SsspParams &p, int e) {
 
 // One batch of up to kRelaxBatch edges per lane: v[j] targets, d[j] offered
 // distances (kInf: none). Returns the mask of entries that entered the next
-// frontier (fresh in this round); entries that dropped to S or more went to
-// the far pile.
+// frontier (fresh in this round); a target that dropped to S or more only
+// has its distance lowered (the far pile is implicit).
 //
 // An offer below the distance read here drops the target's distance in this
 // round whoever's atomicMin lands first (the value read is at most the one
@@ -189,14 +167,8 @@ __device__ __forceinline__ unsigned relax_batch(const SsspParams &p, const int (
     }
   unsigned fresh = 0;
 #pragma unroll
-  for (int j = 0; j < kRelaxBatch; ++j) {
-    if (!(improved >> j & 1u)) continue;
-    if (d[j] < S) {
-      if (atomicExch(p.stamp + v[j], r) != r) fresh |= 1u << j;
-    } else {
-      push_far(p, v[j]);
-    }
-  }
+  for (int j = 0; j < kRelaxBatch; ++j)
+    if ((improved >> j & 1u) && d[j] < S && atomicExch(p.stamp + v[j], r) != r) fresh |= 1u << j;
   return fresh;
 }
 
@@ -384,8 +356,7 @@ __device__ __forceinline__ void sssp_units_by_group(const SsspParams &p, const i
 struct Split {
   unsigned S;      // near: distance below S
   unsigned s;      // a heavy near vertex is relaxed when its distance is below s
-  unsigned S_old;  // (split in progress) far vertices below it are stale
-  unsigned cur;    // current far list
+  unsigned S_old;  // (split in progress) the split before it
 };
 
 __device__ __forceinline__ Split read_split() {
@@ -393,7 +364,6 @@ __device__ __forceinline__ Split read_split() {
   q.S = s_ph.S;
   q.s = s_ph.s;
   q.S_old = s_ph.S_old;
-  q.cur = s_ph.cur;
   return q;
 }
 
@@ -403,88 +373,144 @@ __device__ __forceinline__ bool relaxed_now(const SsspParams &p, const int4 &f, 
   return f.w - f.z <= p.threshold || (unsigned)f.y < s;
 }
 
-// A full warp appends the lanes with `near` set to the next frontier: entry
-// (v, d, first edge, end edge) at a warp-reserved slot, and accounts for the
-// next round: how many entries it relaxes, and the smallest distance of a
-// heavy entry that waits.
-__device__ __forceinline__ void append_near(const SsspParams &p, bool near, int v, unsigned dv, int a, int b,
-                                            unsigned s) {
-  const unsigned nb = __ballot_sync(0xffffffffu, near);
-  if (nb == 0) return;
+// What the entries appended by a thread mean for the next round: how many of
+// them it relaxes, and the smallest distance of a heavy one that waits. Kept
+// in registers and added to the header once per warp at the end of a pass
+// (flush_near), instead of two more same-address atomics per warp step.
+struct NearAcc {
+  unsigned long long elig = 0;
+  unsigned hmin = kInf;
+};
+
+// A full warp appends up to N entries per lane (entry j when bit j of `near`
+// is set) to the next frontier: (v, d, first edge, end edge) at consecutive
+// slots of one reservation per warp step.
+template <int N>
+__device__ __forceinline__ void append_near(const SsspParams &p, unsigned near, const int (&v)[N],
+                                            const unsigned (&dv)[N], const int (&a)[N], const int (&b)[N], unsigned s,
+                                            NearAcc &acc) {
+  const int cnt = __popc(near);
+  const int inc = warp_inclusive_scan(cnt);
+  const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
+  if (total == 0) return;
   unsigned long long base = 0;
-  if (lane_id() == 0) base = atomicAdd(&p.hdr->nf_near, (unsigned long long)__popc(nb));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  const int4 f = make_int4(v, (int)dv, a, b);
-  const bool now = near && relaxed_now(p, f, s);
-  if (near) p.fcur[base + __popc(nb & lanemask_lt())] = f;
-  const unsigned eb = __ballot_sync(0xffffffffu, now);
-  if (eb == nb) {
-    if (lane_id() == 0) atomicAdd(&p.hdr->nf_elig, (unsigned long long)__popc(eb));
-    return;
-  }
-  const unsigned hm = __reduce_min_sync(0xffffffffu, (near && !now) ? dv : kInf);
-  if (lane_id() == 0) {
-    if (eb) atomicAdd(&p.hdr->nf_elig, (unsigned long long)__popc(eb));
-    atomicMin(&p.hdr->nf_hmin, hm);
+  if (lane_id() == kWarp - 1) base = atomicAdd(&p.hdr->nf_near, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, kWarp - 1) + (unsigned long long)(inc - cnt);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (!(near >> j & 1u)) continue;
+    const int4 f = make_int4(v[j], (int)dv[j], a[j], b[j]);
+    p.fcur[base++] = f;
+    if (relaxed_now(p, f, s)) acc.elig++;
+    else if (dv[j] < acc.hmin) acc.hmin = dv[j];
   }
 }
 
-// A full warp appends the lanes with `far` set to far list `list` (each lane's
-// vertex is new to that list).
-__device__ __forceinline__ void append_far(const SsspParams &p, bool far, int v, unsigned list) {
-  const unsigned fb = __ballot_sync(0xffffffffu, far);
-  if (fb == 0) return;
-  unsigned long long base = 0;
-  if (lane_id() == 0) base = atomicAdd(&p.hdr->nf_far[list], (unsigned long long)__popc(fb));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (far) p.far[list][base + __popc(fb & lanemask_lt())] = v;
+__device__ __forceinline__ void flush_near(const SsspParams &p, const NearAcc &acc) {
+  const unsigned long long e = warp_sum(acc.elig);
+  const unsigned h = __reduce_min_sync(0xffffffffu, acc.hmin);
+  if (lane_id() == 0) {
+    if (e) atomicAdd(&p.hdr->nf_elig, e);
+    if (h != kInf) atomicMin(&p.hdr->nf_hmin, h);
+  }
 }
 
 // Commit of one entry of the round's list (called by full warps; `valid`
-// false for lanes past the end): every listed vertex is below the split (the
-// relaxations sent the others to the far pile), so it becomes a next-frontier
-// entry with the distance and edge range it has now.
-__device__ __forceinline__ void commit_vertex(const SsspParams &p, bool valid, int v, const Split &q) {
-  unsigned dv = kInf;
-  int a = 0, b = 0;
+// false for lanes past the end): every listed vertex is below the split (a
+// vertex that dropped to the split or above stayed in the far pile), so it
+// becomes a next-frontier entry with the distance and edge range it has now.
+__device__ __forceinline__ void commit_vertex(const SsspParams &p, bool valid, int v, const Split &q,
+                                              NearAcc &acc) {
+  int vv[1] = {v}, a[1] = {0}, b[1] = {0};
+  unsigned dv[1] = {kInf};
   if (valid) {
-    dv = __ldcg(p.dist + v);
-    a = __ldg(p.off + v);
-    b = __ldg(p.off + v + 1);
+    dv[0] = __ldcg(p.dist + v);
+    a[0] = __ldg(p.off + v);
+    b[0] = __ldg(p.off + v + 1);
   }
-  append_near(p, valid, v, dv, a, b, q.s);
+  append_near<1>(p, valid ? 1u : 0u, vv, dv, a, b, q.s, acc);
 }
 
-// Split, first pass: the smallest distance among far-pile vertices at or
-// above S (the others were relaxed with their distance already).
-__device__ __forceinline__ void split_min_vertex(const SsspParams &p, bool valid, int v, const Split &q) {
-  unsigned dv = kInf;
-  if (valid) {
-    dv = __ldcg(p.dist + v);
-    if (dv < q.S) dv = kInf;
+// The split's passes read every distance, four per 16-byte load when the
+// array allows (the caller's array may start anywhere; then one at a time).
+// Thread t of T takes vertices 4t..4t+3, then 4(t+T).., so a warp reads 512
+// consecutive bytes per step.
+
+// Split, first pass, over every vertex: the smallest finite distance at or
+// above S (the far pile: those vertices dropped to S or more and have not
+// been relaxed since). Called by every thread of a grid of T threads (thread
+// t); one reduction per warp at the end.
+__device__ __forceinline__ void split_min_pass(const SsspParams &p, const Split &q, int t, int T) {
+  unsigned m = kInf;
+  auto take = [&](unsigned dv) {
+    if (dv >= q.S && dv < m) m = dv;  // kInf (unreached) never lowers m
+  };
+  if ((reinterpret_cast<uintptr_t>(p.dist) & 15u) == 0) {
+    const uint4 *d4 = reinterpret_cast<const uint4 *>(p.dist);
+    const int n4 = p.n >> 2;
+    for (int i = t; i < n4; i += T) {
+      const uint4 v = __ldcg(d4 + i);
+      take(v.x);
+      take(v.y);
+      take(v.z);
+      take(v.w);
+    }
+    for (int v = (n4 << 2) + t; v < p.n; v += T) take(__ldcg(p.dist + v));
+  } else {
+    for (int v = t; v < p.n; v += T) take(__ldcg(p.dist + v));
   }
-  const unsigned m = __reduce_min_sync(0xffffffffu, dv);
+  m = __reduce_min_sync(0xffffffffu, m);
   if (lane_id() == 0 && m != kInf) atomicMin(&p.hdr->nf_dmin, m);
 }
 
-// Split, second pass (S and s are the new ones): stale far vertices (below the
-// old S) leave the pile, those below the new S form the next frontier, the
-// rest move to the other far list with the next epoch's mark.
-__device__ __forceinline__ void split_apply_vertex(const SsspParams &p, bool valid, int v, const Split &q,
-                                                   unsigned epoch) {
-  unsigned dv = kInf;
-  int a = 0, b = 0;
-  if (valid) {
-    dv = __ldcg(p.dist + v);
-    a = __ldg(p.off + v);
-    b = __ldg(p.off + v + 1);
+// Split, second pass, over every vertex (S and s are the new ones): the far
+// vertices below the new S (distance in [old S, new S)) form the next
+// frontier. Called by every thread of a grid of T threads (T a multiple of 32).
+__device__ __forceinline__ void split_apply_pass(const SsspParams &p, const Split &q, int t, int T) {
+  NearAcc acc;
+  auto in_bucket = [&](unsigned dv) { return dv >= q.S_old && dv < q.S; };
+  const int base = t - (int)lane_id();  // warp-uniform loops: the appends need the whole warp
+  const bool vec = (reinterpret_cast<uintptr_t>(p.dist) & 15u) == 0;
+  const int n4 = vec ? p.n >> 2 : 0;
+  const uint4 *d4 = reinterpret_cast<const uint4 *>(p.dist);
+  for (int i0 = base; i0 < n4; i0 += T) {
+    const int i = i0 + (int)lane_id();
+    unsigned dv[4] = {kInf, kInf, kInf, kInf};
+    if (i < n4) {
+      const uint4 x = __ldcg(d4 + i);
+      dv[0] = x.x;
+      dv[1] = x.y;
+      dv[2] = x.z;
+      dv[3] = x.w;
+    }
+    unsigned near = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (in_bucket(dv[j])) near |= 1u << j;
+    if (!__any_sync(0xffffffffu, near != 0)) continue;
+    int v[4], a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = 4 * i + j;
+      a[j] = b[j] = 0;
+      if (near >> j & 1u) {
+        a[j] = __ldg(p.off + v[j]);
+        b[j] = __ldg(p.off + v[j] + 1);
+      }
+    }
+    append_near<4>(p, near, v, dv, a, b, q.s, acc);
   }
-  const bool live = valid && dv >= q.S_old;
-  const bool near = live && dv < q.S;
-  append_near(p, near, v, dv, a, b, q.s);
-  const bool keep = live && !near;
-  if (keep) p.fmark[v] = epoch + 1;
-  append_far(p, keep, v, q.cur ^ 1u);
+  for (int v0 = 4 * n4 + base; v0 < p.n; v0 += T) {  // the rest one at a time
+    int v[1] = {v0 + (int)lane_id()}, a[1] = {0}, b[1] = {0};
+    unsigned dv[1] = {v[0] < p.n ? __ldcg(p.dist + v[0]) : kInf};
+    const unsigned near = in_bucket(dv[0]) ? 1u : 0u;
+    if (near) {
+      a[0] = __ldg(p.off + v[0]);
+      b[0] = __ldg(p.off + v[0] + 1);
+    }
+    append_near<1>(p, near, v, dv, a, b, q.s, acc);
+  }
+  flush_near(p, acc);
 }
 
 // The top of the width-w bucket of distance d, at most all ones.
@@ -511,14 +537,14 @@ __device__ __forceinline__ void publish_frontier(const SsspParams &p) {
   h->launches = 0ull;  // the round's children have all finished: their pool slots are free
 }
 
-// The split's new S and s from the smallest live far distance (single
-// thread). Returns false when every far vertex was stale (the pile empties).
+// The split's new S and s from the smallest far distance (single thread).
+// Returns false, and marks the run done, when no vertex is at or above S.
 __device__ __forceinline__ bool advance_split(const SsspParams &p) {
   WsHeader *h = p.hdr;
   const unsigned dmin = ld_volatile(&h->nf_dmin);
   h->nf_dmin = kInf;
   if (dmin == kInf) {
-    h->nf_far[ld_volatile(&h->nf_cur)] = 0ull;
+    h->nf_done = 1u;
     return false;
   }
   h->nf_split_old = ld_volatile(&h->nf_split);
@@ -527,15 +553,8 @@ __device__ __forceinline__ bool advance_split(const SsspParams &p) {
   return true;
 }
 
-// After split_apply: the other far list becomes the current one, the epoch advances.
-__device__ __forceinline__ void finish_split(const SsspParams &p) {
-  WsHeader *h = p.hdr;
-  const unsigned cur = ld_volatile(&h->nf_cur);
-  h->nf_far[cur] = 0ull;
-  h->nf_cur = cur ^ 1u;
-  h->nf_epoch = ld_volatile(&h->nf_epoch) + 1u;
-  publish_frontier(p);
-}
+// After split_apply: the far vertices it took are the next frontier.
+__device__ __forceinline__ void finish_split(const SsspParams &p) { publish_frontier(p); }
 
 }  // namespace
 
@@ -548,7 +567,6 @@ __global__ void __launch_bounds__(1024) sssp_init(SsspParams p) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += G) {
     p.dist[v] = v == p.source ? 0u : kInf;
     p.stamp[v] = kInf;
-    if (p.fmark) p.fmark[v] = kInf;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.fcur[0] = make_int4(p.source, 0, __ldg(p.off + p.source), __ldg(p.off + p.source + 1));
@@ -892,15 +910,13 @@ __global__ void sssp_split_apply(SsspParams p, unsigned r);
 __device__ void continue_after(const SsspParams &p, unsigned next_round) {
   WsHeader *h = p.hdr;
   const unsigned long long nn = ld_volatile(&h->aux[0]);
-  const unsigned long long nfar = ld_volatile(&h->nf_far[ld_volatile(&h->nf_cur)]);
   h->round = next_round;
   __threadfence();
   const bool ok = ld_volatile(&h->status) == 0u;
   if (ok && nn > 0 && next_round < p.max_rounds) {
     launch_parent(p, next_round, (int)nn, cudaStreamTailLaunch);
-  } else if (ok && nn == 0 && nfar > 0) {
-    const int blocks = (int)min((nfar + 255) / 256, (unsigned long long)p.commit_blocks);
-    sssp_split_min<<<blocks > 0 ? blocks : 1, 256, 0, cudaStreamTailLaunch>>>(p, next_round);
+  } else if (ok && nn == 0 && p.delta && !ld_volatile(&h->nf_done)) {
+    sssp_split_min<<<p.commit_blocks, 256, 0, cudaStreamTailLaunch>>>(p, next_round);
   } else {
     if (ok && nn > 0) sssp_fail(p, DPC_ERR_OVERFLOW);  // the round cap was reached with work left
     if (p.stats) p.stats->rounds = next_round;
@@ -918,10 +934,12 @@ __global__ void __launch_bounds__(256) sssp_commit(SsspParams p, unsigned r) {
   const Split q = read_split();
   const int G = gridDim.x * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  NearAcc acc;
   for (int i0 = gtid - (int)lane_id(); i0 < nn; i0 += G) {
     const int i = i0 + (int)lane_id();
-    commit_vertex(p, i < nn, i < nn ? __ldcg(p.fnext + i) : 0, q);
+    commit_vertex(p, i < nn, i < nn ? __ldcg(p.fnext + i) : 0, q, acc);
   }
+  flush_near(p, acc);
   if (!last_block_done(&p.hdr->done_blocks2)) return;
   if (threadIdx.x == 0) {
     publish_frontier(p);
@@ -932,13 +950,7 @@ __global__ void __launch_bounds__(256) sssp_commit(SsspParams p, unsigned r) {
 // The split, first pass (grid-stride over the current far list).
 __global__ void __launch_bounds__(256) sssp_split_min(SsspParams p, unsigned r) {
   phase_sync(p);
-  const Split q = read_split();
-  const int nfar = (int)s_ph.nfar;
-  const int G = gridDim.x * blockDim.x;
-  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x - (int)lane_id(); i0 < nfar; i0 += G) {
-    const int i = i0 + (int)lane_id();
-    split_min_vertex(p, i < nfar, i < nfar ? __ldcg(p.far[q.cur] + i) : 0, q);
-  }
+  split_min_pass(p, read_split(), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   if (!last_block_done(&p.hdr->done_blocks2)) return;
   if (threadIdx.x == 0) {
     const bool live = advance_split(p);
@@ -956,14 +968,8 @@ __global__ void __launch_bounds__(256) sssp_split_min(SsspParams p, unsigned r) 
 // The split, second pass.
 __global__ void __launch_bounds__(256) sssp_split_apply(SsspParams p, unsigned r) {
   phase_sync(p);
-  const Split q = read_split();
-  const unsigned epoch = s_ph.epoch;
-  const int nfar = (int)s_ph.nfar;
-  const int G = gridDim.x * blockDim.x;
-  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x - (int)lane_id(); i0 < nfar; i0 += G) {
-    const int i = i0 + (int)lane_id();
-    split_apply_vertex(p, i < nfar, i < nfar ? __ldcg(p.far[q.cur] + i) : 0, q, epoch);
-  }
+  if (s_ph.done) return;  // (flat level) the split found no vertex at or above S
+  split_apply_pass(p, read_split(), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   if (!last_block_done(&p.hdr->done_blocks2)) return;
   if (threadIdx.x == 0) {
     finish_split(p);
@@ -1045,18 +1051,11 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
     const int nf = (int)s_ph.nf;
     if (nf == 0) {
       // the split: the far pile's smallest live distance, then the new frontier from it
-      const Split q0 = read_split();
-      const int nfar = (int)s_ph.nfar;
-      if (nfar == 0) break;
-      for (int i0 = gtid - lane; i0 < nfar; i0 += G)
-        split_min_vertex(p, i0 + lane < nfar, i0 + lane < nfar ? __ldcg(p.far[q0.cur] + i0 + lane) : 0, q0);
+      if (!p.delta) break;  // no split: an empty frontier ends the run
+      split_min_pass(p, read_split(), gtid, G);
       if (!queue_barrier(p, ++k, kBarSplitMin)) return;
-      const Split q = read_split();
-      if (s_ph.nfar == 0ull) break;  // every far vertex was stale
-      const unsigned epoch = s_ph.epoch;
-      for (int i0 = gtid - lane; i0 < nfar; i0 += G)
-        split_apply_vertex(p, i0 + lane < nfar, i0 + lane < nfar ? __ldcg(p.far[q.cur] + i0 + lane) : 0, q,
-                           epoch);
+      if (s_ph.done) break;  // no vertex at or above the split: every distance is final
+      split_apply_pass(p, read_split(), gtid, G);
       if (!queue_barrier(p, ++k, kBarSplitApply)) return;
       continue;
     }
@@ -1133,8 +1132,10 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
     // commit: the next frontier's entries and the far pile
     const int nn = (int)s_ph.aux1;
     const Split q = read_split();
+    NearAcc acc;
     for (int i0 = gtid - lane; i0 < nn; i0 += G)
-      commit_vertex(p, i0 + lane < nn, i0 + lane < nn ? __ldcg(p.fnext + i0 + lane) : 0, q);
+      commit_vertex(p, i0 + lane < nn, i0 + lane < nn ? __ldcg(p.fnext + i0 + lane) : 0, q, acc);
+    flush_near(p, acc);
     ++r;
     if (!queue_barrier(p, ++k, kBarRound)) return;
   }
@@ -1170,7 +1171,6 @@ size_t sssp_workspace_bytes(int n, int m, dpc_level level, const LaunchCfg &c) {
   b += align_up((size_t)n * sizeof(int4), 256);      // fcur
   b += align_up((size_t)n * sizeof(int), 256);       // fnext
   b += align_up((size_t)n * sizeof(unsigned), 256);  // stamp
-  if (c.delta) b += 2 * align_up((size_t)n * sizeof(int), 256) + align_up((size_t)n * sizeof(unsigned), 256);
   if (level == DPC_WARP || level == DPC_BLOCK || level == DPC_GRID || level == DPC_QUEUE)
     b += align_up(sssp_max_units(n, m, c.threshold, c.chunk) * sizeof(int4), 256);
   return b;
@@ -1186,16 +1186,6 @@ void sssp_carve(SsspParams &p, void *workspace, int n, int m, dpc_level level, c
   b += align_up((size_t)n * sizeof(int), 256);
   p.stamp = reinterpret_cast<unsigned *>(b);
   b += align_up((size_t)n * sizeof(unsigned), 256);
-  p.far[0] = p.far[1] = nullptr;
-  p.fmark = nullptr;
-  if (c.delta) {
-    p.far[0] = reinterpret_cast<int *>(b);
-    b += align_up((size_t)n * sizeof(int), 256);
-    p.far[1] = reinterpret_cast<int *>(b);
-    b += align_up((size_t)n * sizeof(int), 256);
-    p.fmark = reinterpret_cast<unsigned *>(b);
-    b += align_up((size_t)n * sizeof(unsigned), 256);
-  }
   p.units = nullptr;
   p.max_units = 0;
   if (level == DPC_WARP || level == DPC_BLOCK || level == DPC_GRID || level == DPC_QUEUE) {
@@ -1238,10 +1228,11 @@ cudaError_t sssp_launch(SsspParams &p, dpc_level level, cudaStream_t s, unsigned
     return cudaGetLastError();
   }
   // flat: host-driven rounds and splits (no device launches at all); after
-  // every step the frontier size and the far pile's size come back
+  // every step the frontier size (and whether a split found nothing) comes back
   HostScratch &hs = host_scratch();
   unsigned r = 0;
   unsigned long long nf = 1;
+  bool split = false;
   for (;;) {
     if (nf > 0) {
       if (r >= p.max_rounds) break;
@@ -1250,23 +1241,19 @@ cudaError_t sssp_launch(SsspParams &p, dpc_level level, cudaStream_t s, unsigned
       sssp_parent_simple<DPC_FLAT><<<blocks, p.parent_threads, 0, s>>>(p, r);
       sssp_commit<<<p.commit_blocks, 256, 0, s>>>(p, r);
       ++r;
+      split = false;
     } else {
+      if (!p.delta || split) break;  // no split, or a split that found no vertex at or above S
       sssp_split_min<<<p.commit_blocks, 256, 0, s>>>(p, r);
       sssp_split_apply<<<p.commit_blocks, 256, 0, s>>>(p, r);
+      split = true;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(hs.sizes, &p.hdr->aux[0], sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
       return e;
-    if ((e = cudaMemcpyAsync(hs.sizes + 1, p.hdr->nf_far, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                             s)) != cudaSuccess)
-      return e;
-    if ((e = cudaMemcpyAsync(&hs.value, &p.hdr->nf_cur, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     nf = hs.sizes[0];
-    const unsigned long long nfar = hs.sizes[1 + (hs.value & 1)];
-    if (nf == 0 && nfar == 0) break;
   }
   if (rounds_out) *rounds_out = r;
   return cudaSuccess;
