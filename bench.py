@@ -707,6 +707,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------- every application at every level
 
 BASIC_DP_POOL = 1 << 18  # pending-launch pool of the basic-DP process: one child launch per large item
+SSSP_NEARFAR = (200, 8)  # near-far split and sub-split widths for R-MAT 22 (weights up to 1,000)
 
 
 def run_apps(dpc, levels, steps, peak, A=None, x=None):
@@ -741,6 +742,17 @@ def run_apps(dpc, levels, steps, peak, A=None, x=None):
     # runs with the large launch pool of its own process (refused launches are relaxed inline)
     apps["sssp_rmat22"] = bench_sssp(dpc, g22, srcs, "R-MAT scale 22, w in [1,1000], 8 random sources", 5,
                                      flush, levels, oracle_reps=1 if with_oracle else 0)
+    # the same graph and sources with the near-far split (Davidson et al.): width 200, sub-split 8 for
+    # vertices above the threshold; the distances (and so the oracle) are the same
+    nf = dpc.Tuning(delta=SSSP_NEARFAR[0], sub_delta=SSSP_NEARFAR[1])
+    apps["sssp_rmat22_nearfar"] = bench_sssp(
+        dpc, g22, srcs, f"R-MAT scale 22, w in [1,1000], 8 random sources, near-far split width {SSSP_NEARFAR[0]}, "
+        f"sub-split width {SSSP_NEARFAR[1]}", 5, flush, levels, tuning=nf)
+    if with_oracle:
+        o = apps["sssp_rmat22"]["oracle"]
+        apps["sssp_rmat22_nearfar"]["oracle"] = dict(o, note="the oracle's Dijkstra on the same sources")
+        for lv, row in apps["sssp_rmat22_nearfar"]["levels"].items():
+            row["speedup_vs_oracle"] = round(o["ms"] / row["ms"], 2)
     del g22
     g19 = gen.rmat(19, edge_factor=32, seed=6)
     apps["pagerank_rmat19"] = bench_pagerank(

@@ -388,10 +388,181 @@ __device__ __forceinline__ int4 child_unit(const TreeParams &p, int c, int first
 
 }  // namespace
 
+// One top-down level of the queue level: the units [lo, hi) taken by the
+// warps of the calling group (warp-uniform start `wstart`, stride `stride`, a
+// multiple of 32): every child's value set to a leaf's, the units of the
+// children with children appended after the level.
+__device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *units, int nroot, int lo, int hi,
+                                                  int wstart, int stride, bool root_level, int ra, int rb,
+                                                  unsigned long long &visited, unsigned long long &internal) {
+  const int lane = lane_id();
+  for (int i0 = lo + wstart; i0 < hi; i0 += stride) {  // warp-uniform
+    const int i = i0 + lane;
+    int a = 0, b = 0;
+    if (i < hi) {
+      const int4 u = root_level ? root_unit(p, i, ra, rb) : __ldcg(units + i);
+      if (u.x >= 0) {
+        a = u.y;
+        b = u.z;
+      }
+    }
+    visited += b - a;
+    int nb = ceil_div(b - a, kKidBatch);
+    for (int d = kWarp / 2; d >= 1; d >>= 1) nb = max(nb, __shfl_xor_sync(0xffffffffu, nb, d));
+    for (int j = 0; j < nb; ++j) {
+      const int k0 = a + j * kKidBatch;
+      int c[kKidBatch], first[kKidBatch], kc[kKidBatch];
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) c[t] = k0 + t < b ? __ldg(p.cidx + k0 + t) : -1;
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) {
+        first[t] = c[t] >= 0 ? __ldg(p.coff + c[t]) : 0;
+        kc[t] = c[t] >= 0 ? __ldg(p.coff + c[t] + 1) : 0;
+      }
+      int mine = 0;
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) {
+        kc[t] -= first[t];
+        mine += units_for(p, kc[t]);
+      }
+      const int inc = warp_inclusive_scan(mine);
+      int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
+      unsigned long long b0 = 0;
+      if (lane == kWarp - 1 && total) b0 = atomicAdd(&p.hdr->cursor, (unsigned long long)total);
+      const unsigned long long base = (unsigned long long)nroot + __shfl_sync(0xffffffffu, b0, kWarp - 1);
+      if (total && base + (unsigned long long)total > (unsigned long long)p.max_units) {
+        if (lane == 0) tree_fail(p, DPC_ERR_OVERFLOW);  // only when the input is not a tree
+        for (unsigned long long q = base + lane; q < (unsigned long long)p.max_units && q < base + total; q += kWarp)
+          units[q] = make_int4(-1, 0, 0, 0);
+        total = 0;
+      }
+      int pos = total ? (int)base + inc - mine : 0;
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) {
+        if (c[t] >= 0) p.out[c[t]] = 0;
+        const int nu = total && c[t] >= 0 ? units_for(p, kc[t]) : 0;
+        if (nu) internal++;
+        if (nu <= kSmallUnits)
+          for (int q = 0; q < nu; ++q) units[pos + q] = child_unit(p, c[t], first[t], kc[t], q);
+        // the units of larger children: the whole warp writes them, child by child
+        unsigned big = __ballot_sync(0xffffffffu, nu > kSmallUnits);
+        while (big) {
+          const int src = __ffs(big) - 1;
+          big &= big - 1;
+          const int bc = __shfl_sync(0xffffffffu, c[t], src), bf = __shfl_sync(0xffffffffu, first[t], src);
+          const int bk = __shfl_sync(0xffffffffu, kc[t], src), bp = __shfl_sync(0xffffffffu, pos, src);
+          const int bn = __shfl_sync(0xffffffffu, nu, src);
+          for (int q = lane; q < bn; q += kWarp) units[bp + q] = child_unit(p, bc, bf, bk, q);
+        }
+        pos += nu;
+      }
+    }
+  }
+}
+
+// A stretch of consecutive narrow levels run by the calling block alone
+// (block barriers between them), from the units [lo, hi) of level `depth`;
+// stops at the first wide or empty level and publishes where (the depth and
+// that level's units) in the header for the other blocks. Kept out of line
+// so that its registers do not weigh on the wide levels' loop.
+__device__ __noinline__ void queue_narrow_stretch(const TreeParams &p, int nroot, int lo, int hi, int depth,
+                                                  unsigned long long *counts) {
+  __shared__ int s_hi;
+  int4 *const units = reinterpret_cast<int4 *>(p.units);
+  const int narrow = 2 * blockDim.x;
+  const int ra = __ldg(p.coff + p.root), rb = __ldg(p.coff + p.root + 1);
+  unsigned long long visited = 0, internal = 0;
+  while (lo < hi && hi - lo <= narrow && depth < p.n) {
+    queue_visit_level(p, units, nroot, lo, hi, threadIdx.x - lane_id(), blockDim.x, depth == 0, ra, rb, visited,
+                      internal);
+    __syncthreads();  // the level's appends and the cursor are visible to the block
+    if (threadIdx.x == 0) {
+      s_hi = (int)min((unsigned long long)nroot + *reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor),
+                      (unsigned long long)p.max_units);
+      p.level_ends[depth + 2] = s_hi;
+    }
+    __syncthreads();
+    lo = hi;
+    hi = s_hi;
+    ++depth;
+  }
+  if (threadIdx.x == 0) {  // where the stretch stopped, for the other blocks
+    p.hdr->aux[1] = (unsigned long long)depth;
+    p.hdr->aux[2] = (unsigned long long)lo;
+    p.hdr->aux[3] = (unsigned long long)hi;
+  }
+  counts[0] += visited;
+  counts[1] += internal;
+}
+
+// One postwork level: units [a0, a1) combine their children's values into
+// their node's. A node's units are consecutive, so consecutive lanes of one
+// node first combine over the warp and one atomic per node and warp remains.
+template <int OP>
+__device__ __forceinline__ void queue_post_level(const TreeParams &p, const int4 *units, int a0, int a1, int wstart,
+                                                 int stride) {
+  const int lane = lane_id();
+  for (int i0 = a0 + wstart; i0 < a1; i0 += stride) {  // warp-uniform
+    const int i = i0 + lane;
+    int node = -1, a = 0, b = 0;
+    if (i < a1) {
+      const int4 u = __ldcg(units + i);
+      node = u.x;
+      if (node >= 0) {
+        a = u.y;
+        b = u.z;
+      }
+    }
+    unsigned v = 0;  // descendants: sum; heights: max
+    for (int k0 = a; k0 < b; k0 += kKidBatch) {
+      int c[kKidBatch], val[kKidBatch];
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) c[t] = k0 + t < b ? __ldg(p.cidx + k0 + t) : -1;
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) val[t] = c[t] >= 0 ? __ldcg(p.out + c[t]) : 0;
+#pragma unroll
+      for (int t = 0; t < kKidBatch; ++t) {
+        if (c[t] < 0) continue;
+        if (OP == kDescendants) v += 1u + (unsigned)val[t];
+        else v = max(v, 1u + (unsigned)val[t]);
+      }
+    }
+    // segmented inclusive scan over runs of equal nodes
+    const int prev = __shfl_up_sync(0xffffffffu, node, 1);
+    int start = lane == 0 || prev != node ? lane : 0;
+    for (int d = 1; d < kWarp; d <<= 1) start = max(start, __shfl_up_sync(0xffffffffu, start, d));
+    for (int d = 1; d < kWarp; d <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane - d >= start) v = OP == kDescendants ? v + o : max(v, o);
+    }
+    const int next = __shfl_down_sync(0xffffffffu, node, 1);
+    if (node >= 0 && (lane == kWarp - 1 || next != node)) {
+      if (OP == kDescendants) atomicAdd(reinterpret_cast<unsigned *>(p.out) + node, v);
+      else atomicMax(p.out + node, (int)v);
+    }
+  }
+}
+
+// A narrow postwork level run by the calling block alone.
+template <int OP>
+__device__ __forceinline__ void queue_post_level_block(const TreeParams &p, int a0, int a1) {
+  queue_post_level<OP>(p, reinterpret_cast<const int4 *>(p.units), a0, a1, threadIdx.x - lane_id(), blockDim.x);
+  __syncthreads();  // the next narrow level reads these values
+}
+
 // 64 registers: four 256-thread blocks fit per SM, for wide trees whose
 // levels hold millions of units; deep narrow trees run fewer blocks (the host
-// sizes the grid), since their levels are short and every one ends in a
-// grid barrier.
+// sizes the grid), since their levels are short.
+//
+// Narrow levels (at most two units per thread of one block: most levels of a
+// deep tree hold a few units) are not worth a grid barrier each: block 0 runs
+// a stretch of consecutive narrow levels alone, separated by block barriers,
+// while the other blocks wait at one grid barrier; it publishes where it
+// stopped (the depth, and the next level's units) before it arrives. The
+// postwork levels follow the same rule; there every block knows every level's
+// width from the recorded level boundaries, so all agree where a grid barrier
+// is needed: after a level that all blocks ran, and before one that follows
+// levels block 0 ran alone.
 template <int OP>
 __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
   int4 *const units = reinterpret_cast<int4 *>(p.units);
@@ -413,120 +584,38 @@ __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
   int lo = 0, hi = nroot;
   unsigned long long visited = 0, internal = 0;
   while (lo < hi && depth < p.n) {
-    for (int i0 = lo + wbase; i0 < hi; i0 += G) {  // warp-uniform
-      const int i = i0 + lane;
-      int a = 0, b = 0;
-      if (i < hi) {
-        const int4 u = depth == 0 ? root_unit(p, i, ra, rb) : __ldcg(units + i);
-        if (u.x >= 0) {
-          a = u.y;
-          b = u.z;
-        }
+    if (hi - lo <= 2 * (int)blockDim.x) {
+      if (blockIdx.x == 0) {
+        unsigned long long counts[2] = {0, 0};
+        queue_narrow_stretch(p, nroot, lo, hi, depth, counts);
+        visited += counts[0];
+        internal += counts[1];
       }
-      visited += b - a;
-      int nb = ceil_div(b - a, kKidBatch);
-      for (int d = kWarp / 2; d >= 1; d >>= 1) nb = max(nb, __shfl_xor_sync(0xffffffffu, nb, d));
-      for (int j = 0; j < nb; ++j) {
-        const int k0 = a + j * kKidBatch;
-        int c[kKidBatch], first[kKidBatch], kc[kKidBatch];
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) c[t] = k0 + t < b ? __ldg(p.cidx + k0 + t) : -1;
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) {
-          first[t] = c[t] >= 0 ? __ldg(p.coff + c[t]) : 0;
-          kc[t] = c[t] >= 0 ? __ldg(p.coff + c[t] + 1) : 0;
-        }
-        int mine = 0;
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) {
-          kc[t] -= first[t];
-          mine += units_for(p, kc[t]);
-        }
-        const int inc = warp_inclusive_scan(mine);
-        int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
-        unsigned long long b0 = 0;
-        if (lane == kWarp - 1 && total) b0 = atomicAdd(&p.hdr->cursor, (unsigned long long)total);
-        const unsigned long long base = (unsigned long long)nroot + __shfl_sync(0xffffffffu, b0, kWarp - 1);
-        if (total && base + (unsigned long long)total > (unsigned long long)p.max_units) {
-          if (lane == 0) tree_fail(p, DPC_ERR_OVERFLOW);  // only when the input is not a tree
-          for (unsigned long long q = base + lane; q < (unsigned long long)p.max_units && q < base + total;
-               q += kWarp)
-            units[q] = make_int4(-1, 0, 0, 0);
-          total = 0;
-        }
-        int pos = total ? (int)base + inc - mine : 0;
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) {
-          if (c[t] >= 0) p.out[c[t]] = 0;
-          const int nu = total && c[t] >= 0 ? units_for(p, kc[t]) : 0;
-          if (nu) internal++;
-          if (nu <= kSmallUnits)
-            for (int q = 0; q < nu; ++q) units[pos + q] = child_unit(p, c[t], first[t], kc[t], q);
-          // the units of larger children: the whole warp writes them, child by child
-          unsigned big = __ballot_sync(0xffffffffu, nu > kSmallUnits);
-          while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const int bc = __shfl_sync(0xffffffffu, c[t], src), bf = __shfl_sync(0xffffffffu, first[t], src);
-            const int bk = __shfl_sync(0xffffffffu, kc[t], src), bp = __shfl_sync(0xffffffffu, pos, src);
-            const int bn = __shfl_sync(0xffffffffu, nu, src);
-            for (int q = lane; q < bn; q += kWarp) units[bp + q] = child_unit(p, bc, bf, bk, q);
-          }
-          pos += nu;
-        }
-      }
+      if (!tree_barrier(p, ++k, -1, 0)) return;
+      depth = (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->aux[1]);
+      lo = (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->aux[2]);
+      hi = (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->aux[3]);
+      continue;
     }
+    queue_visit_level(p, units, nroot, lo, hi, wbase, G, depth == 0, ra, rb, visited, internal);
     if (!tree_barrier(p, ++k, depth + 2, nroot)) return;
     lo = hi;
     hi = __ldcg(p.level_ends + depth + 2);
     ++depth;
   }
 
-  // postwork bottom-up: level L's units combine their children's values. A
-  // node's units are consecutive, so consecutive lanes of one node first
-  // combine over the warp and one atomic per node and warp remains.
+  // postwork bottom-up
+  const int narrow = 2 * blockDim.x;
+  auto level_narrow = [&](int L) { return __ldcg(p.level_ends + L + 1) - __ldcg(p.level_ends + L) <= narrow; };
   for (int L = depth - 1; L >= 0; --L) {
     const int a0 = __ldcg(p.level_ends + L), a1 = __ldcg(p.level_ends + L + 1);
-    for (int i0 = a0 + wbase; i0 < a1; i0 += G) {  // warp-uniform
-      const int i = i0 + lane;
-      int node = -1, a = 0, b = 0;
-      if (i < a1) {
-        const int4 u = __ldcg(units + i);
-        node = u.x;
-        if (node >= 0) {
-          a = u.y;
-          b = u.z;
-        }
-      }
-      unsigned v = 0;  // descendants: sum; heights: max
-      for (int k0 = a; k0 < b; k0 += kKidBatch) {
-        int c[kKidBatch], val[kKidBatch];
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) c[t] = k0 + t < b ? __ldg(p.cidx + k0 + t) : -1;
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) val[t] = c[t] >= 0 ? __ldcg(p.out + c[t]) : 0;
-#pragma unroll
-        for (int t = 0; t < kKidBatch; ++t) {
-          if (c[t] < 0) continue;
-          if (OP == kDescendants) v += 1u + (unsigned)val[t];
-          else v = max(v, 1u + (unsigned)val[t]);
-        }
-      }
-      // segmented inclusive scan over runs of equal nodes
-      const int prev = __shfl_up_sync(0xffffffffu, node, 1);
-      int start = lane == 0 || prev != node ? lane : 0;
-      for (int d = 1; d < kWarp; d <<= 1) start = max(start, __shfl_up_sync(0xffffffffu, start, d));
-      for (int d = 1; d < kWarp; d <<= 1) {
-        const unsigned o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane - d >= start) v = OP == kDescendants ? v + o : max(v, o);
-      }
-      const int next = __shfl_down_sync(0xffffffffu, node, 1);
-      if (node >= 0 && (lane == kWarp - 1 || next != node)) {
-        if (OP == kDescendants) atomicAdd(reinterpret_cast<unsigned *>(p.out) + node, v);
-        else atomicMax(p.out + node, (int)v);
-      }
+    if (a1 - a0 <= narrow) {
+      if (blockIdx.x == 0) queue_post_level_block<OP>(p, a0, a1);
+      if (L > 0 && !level_narrow(L - 1) && !tree_barrier(p, ++k, -1, 0)) return;
+    } else {
+      queue_post_level<OP>(p, units, a0, a1, wbase, G);
+      if (!tree_barrier(p, ++k, -1, 0)) return;
     }
-    if (!tree_barrier(p, ++k, -1, 0)) return;
   }
   if (p.stats) {
     visited = warp_sum(visited);
