@@ -592,6 +592,22 @@ def bench_serve(count=4096, rate=2000.0, seed=5):
     res = {"workload": f"{count} requests, Poisson {rate:g}/s, 60% SSSP (R-MAT 2^10..2^18), "
                        f"40% TD/TH (trees 1e3..1e6 nodes), pool of {len(graphs)} graphs + {len(trees)} trees",
            "generation_s": round(gen_s, 1)}
+    # the autotuner: a coordinate search over the engine's knobs on a saturated sample of the same mix
+    # (another seed), cached under the mix's key; the capacity sweep below runs the default and the tuned
+    from paper_1606_08150_gb300 import autotune
+
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    t0 = time.time()
+    sample = serve.poisson_stream(np.random.default_rng(seed + 7), 512, 0.0, len(graphs), len(trees), sources)
+    tuned, trials = autotune.tune_engine(graphs, trees, sample, sms)
+    cache = autotune.Cache()
+    cache.store(autotune.mix_key(graphs, trees, 0.6), tuned)
+    res["autotune"] = {"key": autotune.mix_key(graphs, trees, 0.6), "default": autotune.ENGINE_DEFAULT,
+                       "tuned": tuned, "trials": [{"params": t.params, "ms_per_request": round(t.ms, 4)}
+                                                 for t in trials],
+                       "seconds": round(time.time() - t0, 1)}
     for label, r in (("poisson", rate), ("saturated", 0.0)):
         reqs = serve.poisson_stream(np.random.default_rng(seed + 1), count, r, len(graphs), len(trees), sources)
         arr = np.array([q.arrival for q in reqs])
@@ -613,31 +629,35 @@ def bench_serve(count=4096, rate=2000.0, seed=5):
         del srv
         torch_empty_cache()
     # capacity at a stated tail latency: the engine under rising offered load
-    # (one request stream per rate), against one-at-a-time's saturated throughput
-    sweep, best = [], None
-    for r in (2000.0, 4000.0, 8000.0, 10000.0, 12000.0, 14000.0, 16000.0, 32000.0):
-        reqs = serve.poisson_stream(np.random.default_rng(seed + 2), count, r, len(graphs), len(trees), sources)
-        arr = np.array([q.arrival for q in reqs])
-        srv = serve.Server(graphs, trees, waves_per_step=32)
-        srv.run(reqs[:64])
-        srv.reset()
-        eng = srv.run(reqs)
-        le = eng.latencies(arr) * 1e3
-        row = {"offered_req_per_s": r, "req_per_s": round(count / eng.makespan, 1),
-               "p50_ms": round(float(np.percentile(le, 50)), 3), "p99_ms": round(float(np.percentile(le, 99)), 3),
-               "status": eng.status}
-        sweep.append(row)
-        if row["p99_ms"] <= SERVE_P99_MS and (best is None or row["req_per_s"] > best["req_per_s"]):
-            best = row
-        del srv
-        torch_empty_cache()
+    # (one request stream per rate), against one-at-a-time's saturated throughput,
+    # with the engine's default configuration and with the tuned one
     base_cap = res["saturated"]["one_at_a_time"]["req_per_s"]
-    res["load_sweep"] = sweep
-    res["capacity"] = {"p99_bound_ms": SERVE_P99_MS,
-                       "engine_req_per_s": best["req_per_s"] if best else None,
-                       "engine_p99_ms": best["p99_ms"] if best else None,
-                       "one_at_a_time_req_per_s": base_cap,
-                       "ratio": round(best["req_per_s"] / base_cap, 3) if best else None}
+    for name, make in (("default", lambda: serve.Server(graphs, trees, waves_per_step=32)),
+                       ("tuned", lambda: serve.server_from_cache(cache, graphs, trees))):
+        sweep, best = [], None
+        for r in (2000.0, 4000.0, 8000.0, 10000.0, 12000.0, 14000.0, 16000.0, 32000.0):
+            reqs = serve.poisson_stream(np.random.default_rng(seed + 2), count, r, len(graphs), len(trees), sources)
+            arr = np.array([q.arrival for q in reqs])
+            srv = make()
+            srv.run(reqs[:64])
+            srv.reset()
+            eng = srv.run(reqs)
+            le = eng.latencies(arr) * 1e3
+            row = {"offered_req_per_s": r, "req_per_s": round(count / eng.makespan, 1),
+                   "p50_ms": round(float(np.percentile(le, 50)), 3), "p99_ms": round(float(np.percentile(le, 99)), 3),
+                   "status": eng.status}
+            sweep.append(row)
+            if row["p99_ms"] <= SERVE_P99_MS and (best is None or row["req_per_s"] > best["req_per_s"]):
+                best = row
+            del srv
+            torch_empty_cache()
+        key = "" if name == "default" else "_tuned"
+        res["load_sweep" + key] = sweep
+        res["capacity" + key] = {"p99_bound_ms": SERVE_P99_MS,
+                                 "engine_req_per_s": best["req_per_s"] if best else None,
+                                 "engine_p99_ms": best["p99_ms"] if best else None,
+                                 "one_at_a_time_req_per_s": base_cap,
+                                 "ratio": round(best["req_per_s"] / base_cap, 3) if best else None}
     return res
 
 

@@ -372,7 +372,10 @@ dpc_status dpc_engine_init(void *workspace, size_t workspace_bytes, int32_t slot
  * intact; the next step continues where this one stopped. With new_count NULL
  * nothing is admitted. All arguments are fixed device pointers or scalars, so a
  * step can be captured in a CUDA graph and replayed after new admissions are
- * copied into the same arrays. Problems must fit the slot size (n <= max_n,
+ * copied into the same arrays. The engine grid is every block that can be
+ * resident (a cooperative launch), or tuning->parent_blocks when that is
+ * smaller; tuning->threshold and tuning->chunk set the SSSP split of large
+ * frontier vertices into EDGES tasks. Problems must fit the slot size (n <= max_n,
  * m <= max_m). The engine checks every admitted descriptor on the device: one
  * that cannot be valid (unknown kind, a size beyond the slot, a missing array,
  * a source or root out of range, a slot out of range) is not run, its slot

@@ -124,6 +124,17 @@ class Cache:
     def key(app: str, level: str, size: int) -> str:
         return f"{app}/{level}/2^{max(0, int(size).bit_length() - 1)}"
 
+    def lookup(self, key: str) -> Optional[Dict[str, int]]:
+        """The raw parameters stored under `key` (any workload key), or None."""
+        p = self.table.get(key)
+        return dict(p) if p is not None else None
+
+    def store(self, key: str, params: Dict[str, int]) -> None:
+        self.table[key] = dict(params)
+        if self.path:
+            with open(self.path, "w") as f:
+                json.dump(self.table, f, indent=1, sort_keys=True)
+
     def get(self, app: str, level: str, size: int) -> Optional[dpc.Tuning]:
         p = self.table.get(self.key(app, level, size))
         return dpc.Tuning(**p) if p is not None else None
@@ -148,3 +159,77 @@ def default_space(app: str, level: str) -> List[Dict[str, int]]:
     if app == "sssp":
         return grid_space(threshold=(16, 32, 64), chunk=(128, 256, 1024), kc=(KC_RULE.get(level, 1),))
     return grid_space(chunk=(8, 32, 128), child_threads=(128, 256), kc=(KC_RULE.get(level, 1),))
+
+
+# ---------------------------------------------------------------- the batched engine
+
+# The engine's knobs: threshold and chunk (how a large SSSP frontier vertex is
+# split into EDGES tasks), the cooperative grid (parent_blocks, 0 = every
+# resident block) and the waves an engine step runs before it returns to the
+# request loop (waves). The default is the engine's own configuration.
+ENGINE_DEFAULT = {"threshold": 32, "chunk": 256, "parent_blocks": 0, "waves": 32}
+
+
+def engine_axes(sms: int) -> Dict[str, Sequence[int]]:
+    """Values tried per knob (coordinate search around the default)."""
+    return {"threshold": (16, 32, 64), "chunk": (128, 256, 512), "parent_blocks": (0, 2 * sms, sms),
+            "waves": (16, 32, 64)}
+
+
+def engine_tuning(params: Dict[str, int]) -> dpc.Tuning:
+    return dpc.Tuning(threshold=params["threshold"], chunk=params["chunk"], parent_blocks=params["parent_blocks"])
+
+
+def mix_key(graphs, trees, sssp_fraction: float) -> str:
+    """Cache key of a request mix: the SSSP share and the size classes of the
+    resident graphs and trees."""
+    gs = sorted({max(0, int(g.n).bit_length() - 1) for g in graphs})
+    ts = sorted({max(0, int(t.n).bit_length() - 1) for t in trees})
+    return (f"engine/sssp{int(round(100 * sssp_fraction))}/graphs2^{gs[0]}-2^{gs[-1]}/"
+            f"trees2^{ts[0]}-2^{ts[-1]}" if gs and ts else "engine/empty")
+
+
+def engine_throughput(graphs, trees, requests, params: Dict[str, int], slots: Optional[int] = None) -> float:
+    """Requests per second of the engine serving `requests` with `params`
+    (the arrivals as given; all at time 0 measures saturated throughput)."""
+    from . import serve
+
+    srv = serve.Server(graphs, trees, slots=slots, waves_per_step=params["waves"], tuning=engine_tuning(params))
+    srv.run(requests[: min(32, len(requests))])  # warm-up: graph capture, module load
+    srv.reset()
+    res = srv.run(requests)
+    if res.status != 0:
+        raise RuntimeError(f"engine status {res.status} with {params}")
+    return len(requests) / res.makespan
+
+
+def tune_engine(graphs, trees, requests, sms: int, slots: Optional[int] = None, sweeps: int = 2
+                ) -> Tuple[Dict[str, int], List[Trial]]:
+    """Coordinate search over the engine's knobs on a request sample: starting
+    from the default, each knob in turn takes the value with the highest
+    throughput, the others fixed, for `sweeps` sweeps (or until nothing
+    changes). Returns the best parameters and every trial (ms per request)."""
+    best = dict(ENGINE_DEFAULT)
+    seen: Dict[Tuple, float] = {}
+    trials: List[Trial] = []
+
+    def measure(p):
+        k = tuple(sorted(p.items()))
+        if k not in seen:
+            seen[k] = engine_throughput(graphs, trees, requests, p, slots)
+            trials.append(Trial(dict(p), 1e3 / seen[k]))
+        return seen[k]
+
+    best_rate = measure(best)
+    axes = engine_axes(sms)
+    for _ in range(sweeps):
+        changed = False
+        for knob, values in axes.items():
+            for v in values:
+                cand = dict(best, **{knob: v})
+                rate = measure(cand)
+                if rate > best_rate * 1.02:  # a clear gain only: the rates carry a few % of noise
+                    best, best_rate, changed = cand, rate, True
+        if not changed:
+            break
+    return best, trials

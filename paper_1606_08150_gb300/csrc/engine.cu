@@ -957,8 +957,11 @@ dpc_status dpc_engine_step(void *workspace, size_t workspace_bytes, int32_t slot
   if (!workspace || workspace_bytes < L.total) return DPC_ERR_WORKSPACE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DPC_ERR_CUDA;
-  const int blocks = engine_grid(dev);
-  if (blocks <= 0) return DPC_ERR_CUDA;
+  const int full = engine_grid(dev);
+  if (full <= 0) return DPC_ERR_CUDA;
+  // every block must be resident (cooperative launch): at most all of them, fewer on request
+  const int blocks = (tuning && tuning->parent_blocks > 0 && tuning->parent_blocks < full) ? tuning->parent_blocks
+                                                                                          : full;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (stats && cudaMemsetAsync(stats, 0, sizeof(dpc_stats), s) != cudaSuccess) return DPC_ERR_CUDA;
   Engine e = engine_view(workspace, slots, L, slot_state, stats);

@@ -212,6 +212,17 @@ class Server:
         return ServeResult(admitted, finished, steps, self.slots, makespan, dpc.read_stats(self.stats).status, slot_of)
 
 
+def server_from_cache(cache, graphs: Sequence[Resident], trees: Sequence[Resident], sssp_fraction: float = 0.6,
+                      **kw) -> "Server":
+    """A Server configured by the autotuner's entry for this request mix
+    (autotune.tune_engine, stored under autotune.mix_key); the engine's
+    default configuration when the cache holds none."""
+    from . import autotune
+
+    p = cache.lookup(autotune.mix_key(graphs, trees, sssp_fraction)) or dict(autotune.ENGINE_DEFAULT)
+    return Server(graphs, trees, waves_per_step=p["waves"], tuning=autotune.engine_tuning(p), **kw)
+
+
 def one_at_a_time(graphs: Sequence[Resident], trees: Sequence[Resident], requests: Sequence[Request],
                   level="grid", on_done=None) -> ServeResult:
     """Baseline: each request is one library call, waited for before the next."""

@@ -27,3 +27,23 @@ def test_cache_keys_by_size_class_and_persists(tmp_path):
 def test_default_spaces_use_the_kc_rule():
     for level, x in autotune.KC_RULE.items():
         assert any(cfg.get("kc") == x for cfg in autotune.default_space("spmv", level))
+
+
+def test_cache_lookup_and_store_raw_params(tmp_path):
+    p = tmp_path / "t.json"
+    c = autotune.Cache(str(p))
+    assert c.lookup("engine/x") is None
+    c.store("engine/x", {"threshold": 16, "chunk": 512, "parent_blocks": 0, "waves": 64})
+    assert autotune.Cache(str(p)).lookup("engine/x")["waves"] == 64
+
+
+def test_mix_key_and_engine_tuning():
+    from types import SimpleNamespace
+
+    graphs = [SimpleNamespace(n=1 << 10), SimpleNamespace(n=(1 << 18) + 5)]
+    trees = [SimpleNamespace(n=1000), SimpleNamespace(n=1_000_000)]
+    assert autotune.mix_key(graphs, trees, 0.6) == "engine/sssp60/graphs2^10-2^18/trees2^9-2^19"
+    t = autotune.engine_tuning(dict(autotune.ENGINE_DEFAULT, parent_blocks=304))
+    assert (t.threshold, t.chunk, t.parent_blocks) == (32, 256, 304)
+    axes = autotune.engine_axes(152)
+    assert all(autotune.ENGINE_DEFAULT[k] in v for k, v in axes.items())

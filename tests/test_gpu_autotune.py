@@ -37,3 +37,63 @@ def test_kc_study_and_tuned_result_on_tree_descendants(dpc):
     run("grid", tuned)
     torch.cuda.synchronize()
     assert np.array_equal(u32(out), oracle.tree_descendants(t.coff, t.cidx, 0))
+
+
+def test_tuned_engine_serves_the_mix_bit_exact(dpc):
+    """The autotuner's coordinate search over the engine's knobs (threshold,
+    chunk, grid size, waves per step) on a saturated sample, stored under the
+    mix's key; the server built from that entry gives every request the
+    oracle's result."""
+    from paper_1606_08150_gb300 import serve
+
+    rng = np.random.default_rng(31)
+    graphs_h = [gen.rmat(s, seed=500 + s) for s in (9, 11, 13)]
+    trees_h = [gen.tree(n, seed=600 + i) for i, n in enumerate((2000, 40000))]
+    graphs = [serve.upload_graph(g) for g in graphs_h]
+    trees = [serve.upload_tree(t) for t in trees_h]
+    sources = [np.nonzero(np.diff(g.off) > 0)[0] for g in graphs_h]
+    sample = serve.poisson_stream(rng, 96, 0.0, len(graphs), len(trees), sources)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    best, trials = autotune.tune_engine(graphs, trees, sample, sms, slots=8, sweeps=1)
+    assert set(best) == set(autotune.ENGINE_DEFAULT) and len(trials) >= 4
+    assert min(t.ms for t in trials) <= [t.ms for t in trials if t.params == autotune.ENGINE_DEFAULT][0]
+    cache = autotune.Cache()
+    cache.store(autotune.mix_key(graphs, trees, 0.6), best)
+    srv = serve.server_from_cache(cache, graphs, trees, slots=8)
+    assert srv.waves == best["waves"]
+    reqs = serve.poisson_stream(rng, 80, 20000.0, len(graphs), len(trees), sources)
+    got = {}
+
+    def keep(i, s):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        got[i] = srv.out[s, :n].cpu().numpy().copy()
+
+    assert srv.run(reqs, on_done=keep).status == 0
+    for i, r in enumerate(reqs):
+        if r.kind == dpc.JOB_SSSP:
+            g = graphs_h[r.problem]
+            want = oracle.sssp_dijkstra(g.off, g.col, g.w, r.source).view(np.int32)
+        elif r.kind == dpc.JOB_TREE_DESCENDANTS:
+            want = oracle.tree_descendants(trees_h[r.problem].coff, trees_h[r.problem].cidx, 0).view(np.int32)
+        else:
+            want = oracle.tree_height(trees_h[r.problem].coff, trees_h[r.problem].cidx, 0)
+        assert np.array_equal(got[i], want), i
+
+
+def test_engine_grid_size_from_tuning(dpc):
+    """A smaller cooperative engine grid (tuning.parent_blocks) runs the same problems to the same results."""
+    from tests.test_gpu_engine import Eng, make_problems, to_jobs, check
+
+    probs = make_problems(5, 10)
+    jobs, keep, outs = to_jobs(dpc, probs)
+    max_n = max(p[1].n for p in probs)
+    max_m = max(p[1].m if p[0] == "sssp" else p[1].n for p in probs)
+    for blocks in (1, 7, 152):
+        for o in outs:
+            o.fill_(-5)
+        e = Eng(dpc, len(jobs), max_n, max_m, tuning=dpc.Tuning(parent_blocks=blocks))
+        e.stage(jobs, list(range(len(jobs))))
+        e.step(1 << 30)
+        torch.cuda.synchronize()
+        assert dpc.read_stats(e.stats).status == 0
+        check(probs, outs)
