@@ -271,6 +271,8 @@ dpc_status dpc_spmv_csr(const int32_t *off, const int32_t *col, const float *val
   p.x = x;
   p.y = y;
   p.nrows = nrows;
+  p.ncols = ncols;
+  p.nnz = nnz;
   p.threshold = c.threshold;
   p.chunk = c.chunk;
   p.child_blocks = c.child_blocks;
@@ -360,6 +362,8 @@ dpc_status dpc_pagerank(const int32_t *in_off, const int32_t *in_src, const int3
   p.val = nullptr;
   p.x = reinterpret_cast<float *>(ws + L.contrib);
   p.nrows = n;
+  p.ncols = n;
+  p.nnz = m;
   p.threshold = c.threshold;
   p.chunk = c.chunk;
   p.child_blocks = c.child_blocks;
@@ -592,6 +596,7 @@ dpc_status dpc_sssp(const int32_t *off, const int32_t *col, const uint32_t *w, i
   p.w = w;
   p.dist = dist;
   p.n = n;
+  p.m = m;
   p.source = source;
   p.threshold = c.threshold;
   p.chunk = c.chunk;

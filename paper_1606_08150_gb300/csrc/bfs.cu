@@ -63,7 +63,7 @@ __device__ __forceinline__ int relax_unit(const BfsParams &p, int2 u, unsigned d
     const int e = a + lane + q * kWarp;
     w[q] = -1;
     if (e < b) {
-      w[q] = __ldg(p.col + e);
+      w[q] = checked_index(__ldg(p.col + e), p.n, &p.hdr->status);
       ++scanned;
     }
   }
@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(1024) bfs_visit_vertex(BfsParams p, int v, uns
   unsigned long long launched = 0, failed = 0, scanned = 0;
   for (int e = a + blockIdx.x * blockDim.x + threadIdx.x; e < b; e += gridDim.x * blockDim.x) {
     scanned++;
-    const int u = __ldg(p.col + e);
+    const int u = checked_index(__ldg(p.col + e), p.n, &p.hdr->status);
+    if (kCheckedBuild && u < 0) continue;
     if (!(nd < __ldcg(p.level + u) && nd < atomicMin(p.level + u, nd))) continue;
     const int deg = __ldg(p.off + u + 1) - __ldg(p.off + u);
     if (deg == 0) continue;
@@ -342,7 +343,8 @@ __global__ void __launch_bounds__(1024) bfs_flat_level(BfsParams p, const int *f
     const int a = __ldg(p.off + v), b = __ldg(p.off + v + 1);
     scanned += (unsigned long long)(b - a);
     for (int e = a; e < b; ++e) {
-      const int u = __ldg(p.col + e);
+      const int u = checked_index(__ldg(p.col + e), p.n, &p.hdr->status);
+      if (kCheckedBuild && u < 0) continue;
       if (nd < __ldcg(p.level + u) && nd < atomicMin(p.level + u, nd)) {
         const unsigned long long pos = atomicAdd(&p.hdr->cursor2, 1ull);
         next[pos] = u;

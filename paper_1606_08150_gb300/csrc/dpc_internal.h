@@ -79,6 +79,8 @@ struct SpmvParams {
   const float *x;
   float *y;
   int nrows;
+  int ncols;          // entries of x (column indices are below it)
+  int nnz;            // entries of col (and val): row ranges lie in [0, nnz]
   int threshold;
   int chunk;
   int max_units;
@@ -215,6 +217,7 @@ struct SsspParams {
   const unsigned *w;
   unsigned *dist;
   int n;
+  int m;
   int source;
   int threshold;
   int chunk;

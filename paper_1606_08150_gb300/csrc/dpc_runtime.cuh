@@ -29,6 +29,40 @@ __device__ __forceinline__ void set_status(unsigned *status, unsigned code) {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & (kWarp - 1); }
 
+// The bounds-checked build (compiled with -DDPC_CHECKED; the library's second
+// build, a stand-in for a memory checker): every index read from the caller's
+// arrays and every append into a bounded buffer goes through checked(), which
+// records DPC_ERR_OVERFLOW in the status word and tells the caller to skip the
+// access when the index is out of range. In the regular build checked() is
+// the constant true and the compiler removes it.
+#ifdef DPC_CHECKED
+constexpr bool kCheckedBuild = true;
+#else
+constexpr bool kCheckedBuild = false;
+#endif
+
+__device__ __forceinline__ bool checked(long long i, long long bound, unsigned *status) {
+  if (!kCheckedBuild) return true;
+  if (i >= 0 && i < bound) return true;
+  set_status(status, DPC_ERR_OVERFLOW);
+  return false;
+}
+
+// An index loaded from a caller's array (a column, a child id): itself, or -1
+// (the kernels' "no entry") when the checked build finds it out of range.
+__device__ __forceinline__ int checked_index(int v, int bound, unsigned *status) {
+  return checked(v, bound, status) ? v : -1;
+}
+
+// An edge range [a, b) read from a caller's offsets: itself, or empty when
+// the checked build finds it outside [0, m].
+__device__ __forceinline__ void checked_range(int &a, int &b, long long m, unsigned *status) {
+  if (!kCheckedBuild) return;
+  if (a >= 0 && a <= b && b <= m) return;
+  set_status(status, DPC_ERR_OVERFLOW);
+  a = b = 0;
+}
+
 // Bounded waits. Every spin on a word that another block writes gives up once
 // kWaitLimitNs of %globaltimer time have passed, or after kWaitPollCap polls
 // should the clock not advance; the caller then reports DPC_ERR_TIMEOUT. A

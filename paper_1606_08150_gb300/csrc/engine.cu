@@ -203,7 +203,7 @@ __device__ __forceinline__ void sssp_relax_edges(const Engine &e, int s, const S
       d[q] = kInfU;
       if (ed < b) {
         const unsigned long long nd = (unsigned long long)du + __ldcs(w + ed);
-        vv[q] = __ldcs(col + ed);
+        vv[q] = checked_index(__ldcs(col + ed), e.slots[s].job.n, &e.hdr->status);
         if (nd >= kInfU) eng_fail(e, DPC_ERR_OVERFLOW);
         else d[q] = (unsigned)nd;
       }
@@ -275,7 +275,7 @@ __device__ __forceinline__ void sssp_relax_edges_staged(const Engine &e, int s, 
       d[q] = kInfU;
       if (ed < b) {
         const unsigned long long nd = (unsigned long long)du + __ldcs(w + ed);
-        vv[q] = __ldcs(col + ed);
+        vv[q] = checked_index(__ldcs(col + ed), e.slots[s].job.n, &e.hdr->status);
         if (nd >= kInfU) eng_fail(e, DPC_ERR_OVERFLOW);
         else d[q] = (unsigned)nd;
       }
@@ -515,7 +515,8 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
       }
       int c[kEngTreeChunk], first[kEngTreeChunk], kc[kEngTreeChunk];
 #pragma unroll
-      for (int j = 0; j < kEngTreeChunk; ++j) c[j] = a + j < b ? __ldg(job.col + a + j) : -1;
+      for (int j = 0; j < kEngTreeChunk; ++j)
+        c[j] = a + j < b ? checked_index(__ldg(job.col + a + j), job.n, &e.hdr->status) : -1;
 #pragma unroll
       for (int j = 0; j < kEngTreeChunk; ++j) {
         first[j] = c[j] >= 0 ? __ldg(job.off + c[j]) : 0;
@@ -576,7 +577,8 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
       }
       int c[kEngTreeChunk], val[kEngTreeChunk];
 #pragma unroll
-      for (int j = 0; j < kEngTreeChunk; ++j) c[j] = a + j < b ? __ldg(job.col + a + j) : -1;
+      for (int j = 0; j < kEngTreeChunk; ++j)
+        c[j] = a + j < b ? checked_index(__ldg(job.col + a + j), job.n, &e.hdr->status) : -1;
 #pragma unroll
       for (int j = 0; j < kEngTreeChunk; ++j) val[j] = c[j] >= 0 ? __ldcg(out + c[j]) : 0;
       unsigned sum = 0;

@@ -51,7 +51,7 @@ __device__ __forceinline__ bool outranked(const GcParams &p, int v, unsigned pv,
 #pragma unroll
     for (int q = 0; q < kScanBatch; ++q) {
       const int e = e0 + q * T;
-      u[q] = e < b ? __ldg(p.col + e) : -1;
+      u[q] = e < b ? checked_index(__ldg(p.col + e), p.n, &p.hdr->status) : -1;
       if (e < b) ++*scanned;
     }
     int c[kScanBatch];
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(1024) gc_vertex_child(GcParams p, int v, int r
   const int a = __ldg(p.off + v), b = __ldg(p.off + v + 1);
   const int e = a + blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= b) return;
-  const int u = __ldg(p.col + e);
+  const int u = checked_index(__ldg(p.col + e), p.n, &p.hdr->status);
+  if (kCheckedBuild && u < 0) return;
   const unsigned pv = __ldg(p.prio + v), pu = __ldg(p.prio + u);
   const int c = __ldcg(p.color + u);
   if (u != v && (c == 0 || c == r) && (pu > pv || (pu == pv && u > v))) p.blocked[v] = (unsigned)r;

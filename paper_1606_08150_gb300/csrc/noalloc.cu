@@ -161,6 +161,8 @@ extern "C" dpc_status dpc_spmv_csr_noalloc(const int32_t *off, const int32_t *co
   p.x = x;
   p.y = y;
   p.nrows = nrows;
+  p.ncols = ncols;
+  p.nnz = nnz;
   p.threshold = c.threshold;
   p.chunk = c.chunk;
   p.child_blocks = c.child_blocks;

@@ -57,6 +57,7 @@ __device__ __forceinline__ void spmv_fail(const SpmvParams &p, unsigned code) {
 // two per term; the sum is still taken strictly left to right.
 template <int MODE>
 __device__ __forceinline__ float seq_dot(const SpmvParams &p, int a, int b) {
+  checked_range(a, b, p.nnz, &p.hdr->status);
   float s = 0.f;
   int k = a;
   for (; k + 8 <= b; k += 8) {
@@ -64,11 +65,12 @@ __device__ __forceinline__ float seq_dot(const SpmvParams &p, int a, int b) {
     float v[8], xv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      c[j] = __ldg(p.col + k + j);
+      c[j] = checked_index(__ldg(p.col + k + j), p.ncols, &p.hdr->status);
       v[j] = MODE == kModeSpmv ? __ldg(p.val + k + j) : 1.f;
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) xv[j] = MODE == kModeSpmv ? __ldg(p.x + c[j]) : __ldcg(p.x + c[j]);
+    for (int j = 0; j < 8; ++j)
+      xv[j] = kCheckedBuild && c[j] < 0 ? 0.f : (MODE == kModeSpmv ? __ldg(p.x + c[j]) : __ldcg(p.x + c[j]));
 #pragma unroll
     for (int j = 0; j < 8; ++j) s = MODE == kModeSpmv ? fmaf(v[j], xv[j], s) : s + xv[j];
   }
@@ -78,11 +80,13 @@ __device__ __forceinline__ float seq_dot(const SpmvParams &p, int a, int b) {
     const int r = b - k;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      c[j] = j < r ? __ldg(p.col + k + j) : 0;
+      c[j] = j < r ? checked_index(__ldg(p.col + k + j), p.ncols, &p.hdr->status) : 0;
       v[j] = MODE == kModeSpmv ? (j < r ? __ldg(p.val + k + j) : 0.f) : 1.f;
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) xv[j] = j < r ? (MODE == kModeSpmv ? __ldg(p.x + c[j]) : __ldcg(p.x + c[j])) : 0.f;
+    for (int j = 0; j < 8; ++j)
+      xv[j] = j < r && !(kCheckedBuild && c[j] < 0) ? (MODE == kModeSpmv ? __ldg(p.x + c[j]) : __ldcg(p.x + c[j]))
+                                                      : 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       if (j < r) s = MODE == kModeSpmv ? fmaf(v[j], xv[j], s) : s + xv[j];
@@ -101,6 +105,7 @@ constexpr int kDotBatch = 16;
 
 template <int MODE>
 __device__ __forceinline__ float group_dot(const SpmvParams &p, int a, int b, int t, int T) {
+  checked_range(a, b, p.nnz, &p.hdr->status);
   float acc = 0.f;
   for (int i0 = a + t; i0 < b; i0 += kDotBatch * T) {
     int c[kDotBatch];
@@ -108,7 +113,7 @@ __device__ __forceinline__ float group_dot(const SpmvParams &p, int a, int b, in
 #pragma unroll
     for (int j = 0; j < kDotBatch; ++j) {
       const int i = i0 + j * T;
-      c[j] = i < b ? __ldcs(p.col + i) : -1;
+      c[j] = i < b ? checked_index(__ldcs(p.col + i), p.ncols, &p.hdr->status) : -1;
       v[j] = MODE == kModeSpmv ? (i < b ? __ldcs(p.val + i) : 0.f) : 1.f;
     }
 #pragma unroll
@@ -126,7 +131,8 @@ __device__ __forceinline__ void spmv_unit(const SpmvParams &p, int4 u) {
   const int lane = lane_id();
   const int row = u.x, k = u.y, nun = u.z, first = u.w;
   if (row < 0) return;  // placeholder written after a buffer overflow
-  const int r0 = __ldg(p.off + row), r1 = __ldg(p.off + row + 1);
+  int r0 = __ldg(p.off + row), r1 = __ldg(p.off + row + 1);
+  checked_range(r0, r1, p.nnz, &p.hdr->status);
   const int a = r0 + k * p.chunk;
   const int b = min(r1, a + p.chunk);
   float s = warp_sum(group_dot<MODE>(p, a, b, lane, kWarp));
@@ -219,10 +225,13 @@ template <int MODE>
 __global__ void __launch_bounds__(1024) spmv_flat(SpmvParams p) {
   const int G = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < p.nrows; r += G) {
-    const int a = __ldg(p.off + r), b = __ldg(p.off + r + 1);
+    int a = __ldg(p.off + r), b = __ldg(p.off + r + 1);
+    checked_range(a, b, p.nnz, &p.hdr->status);
     float s = 0.f;
     for (int k = a; k < b; ++k) {
-      const float xv = MODE == kModeSpmv ? __ldg(p.x + __ldg(p.col + k)) : __ldcg(p.x + __ldg(p.col + k));
+      const int c = checked_index(__ldg(p.col + k), p.ncols, &p.hdr->status);
+      if (kCheckedBuild && c < 0) continue;
+      const float xv = MODE == kModeSpmv ? __ldg(p.x + c) : __ldcg(p.x + c);
       s = MODE == kModeSpmv ? fmaf(__ldg(p.val + k), xv, s) : s + xv;
     }
     p.y[r] = row_result<MODE>(p, s);

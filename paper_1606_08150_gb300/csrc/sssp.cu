@@ -109,10 +109,11 @@ __device__ __forceinline__ void push_next(const SsspParams &p, int v, unsigned r
   unsigned long long base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(&p.hdr->cursor2, (unsigned long long)g.size());
   base = g.shfl(base, 0);
-  p.fnext[base + g.thread_rank()] = v;
+  if (checked(base + g.thread_rank(), p.n, &p.hdr->status)) p.fnext[base + g.thread_rank()] = v;
 }
 
 __device__ __forceinline__ void relax(const SsspParams &p, int v, unsigned du, unsigned w, unsigned r, unsigned S) {
+  if (!checked(v, p.n, &p.hdr->status)) return;
   const unsigned long long nd = (unsigned long long)du + w;
   if (nd >= kInf) {
     sssp_fail(p, DPC_ERR_OVERFLOW);
@@ -200,7 +201,7 @@ __device__ __forceinline__ void relax_edges(const SsspParams &p, int a, int b, u
       d[j] = kInf;
       if (e < b) {
         const unsigned long long nd = (unsigned long long)du + edge_w(p, e);
-        v[j] = edge_col(p, e);
+        v[j] = checked_index(edge_col(p, e), p.n, &p.hdr->status);
         if (nd >= kInf) sssp_fail(p, DPC_ERR_OVERFLOW);
         else d[j] = (unsigned)nd;
       }
@@ -215,7 +216,7 @@ __device__ __forceinline__ void relax_edges(const SsspParams &p, int a, int b, u
     base = g.shfl(base, 0) + excl;
 #pragma unroll
     for (int j = 0; j < kRelaxBatch; ++j)
-      if (fresh >> j & 1u) p.fnext[base++] = v[j];
+      if ((fresh >> j & 1u) && checked(base, p.n, &p.hdr->status)) p.fnext[base++] = v[j];
   }
 }
 
@@ -241,7 +242,8 @@ __device__ __forceinline__ void stage_flush(const SsspParams &p, const WarpStage
   unsigned long long base = 0;
   if (lane_id() == 0) base = atomicAdd(&p.hdr->cursor2, (unsigned long long)c);
   base = __shfl_sync(0xffffffffu, base, 0);
-  for (int i = lane_id(); i < c; i += kWarp) p.fnext[base + i] = ws.buf[i];
+  for (int i = lane_id(); i < c; i += kWarp)
+    if (checked(base + i, p.n, &p.hdr->status)) p.fnext[base + i] = ws.buf[i];
   __syncwarp();
   if (lane_id() == 0) *ws.cnt = 0;
   __syncwarp();
@@ -263,7 +265,7 @@ __device__ __forceinline__ void stage_batch(const SsspParams &p, const WarpStage
   int pos = *ws.cnt + inc - cnt;
 #pragma unroll
   for (int j = 0; j < kRelaxBatch; ++j)
-    if (fresh >> j & 1u) ws.buf[pos++] = v[j];
+    if ((fresh >> j & 1u) && checked(pos, kStage, &p.hdr->status)) ws.buf[pos++] = v[j];
   __syncwarp();
   if (lane_id() == kWarp - 1) *ws.cnt += total;
   __syncwarp();
@@ -283,7 +285,7 @@ __device__ __forceinline__ void relax_edges_staged(const SsspParams &p, int a, i
       d[j] = kInf;
       if (e < b) {
         const unsigned long long nd = (unsigned long long)du + edge_w(p, e);
-        v[j] = edge_col(p, e);
+        v[j] = checked_index(edge_col(p, e), p.n, &p.hdr->status);
         if (nd >= kInf) sssp_fail(p, DPC_ERR_OVERFLOW);
         else d[j] = (unsigned)nd;
       }
@@ -325,7 +327,7 @@ __device__ __forceinline__ void relax_inline_warp(const SsspParams &p, int a, in
       d[j] = kInf;
       if (k < total) {
         const unsigned long long nd = (unsigned long long)dl + edge_w(p, e);
-        v[j] = edge_col(p, e);
+        v[j] = checked_index(edge_col(p, e), p.n, &p.hdr->status);
         if (nd >= kInf) sssp_fail(p, DPC_ERR_OVERFLOW);
         else d[j] = (unsigned)nd;
       }
@@ -400,7 +402,7 @@ __device__ __forceinline__ void append_near(const SsspParams &p, unsigned near, 
   for (int j = 0; j < N; ++j) {
     if (!(near >> j & 1u)) continue;
     const int4 f = make_int4(v[j], (int)dv[j], a[j], b[j]);
-    p.fcur[base++] = f;
+    if (checked(base, p.n, &p.hdr->status)) p.fcur[base++] = f;
     if (relaxed_now(p, f, s)) acc.elig++;
     else if (dv[j] < acc.hmin) acc.hmin = dv[j];
   }
@@ -427,6 +429,7 @@ __device__ __forceinline__ void commit_vertex(const SsspParams &p, bool valid, i
     dv[0] = __ldcg(p.dist + v);
     a[0] = __ldg(p.off + v);
     b[0] = __ldg(p.off + v + 1);
+    checked_range(a[0], b[0], p.m, &p.hdr->status);
   }
   append_near<1>(p, valid ? 1u : 0u, vv, dv, a, b, q.s, acc);
 }
@@ -496,6 +499,7 @@ __device__ __forceinline__ void split_apply_pass(const SsspParams &p, const Spli
       if (near >> j & 1u) {
         a[j] = __ldg(p.off + v[j]);
         b[j] = __ldg(p.off + v[j] + 1);
+        checked_range(a[j], b[j], p.m, &p.hdr->status);
       }
     }
     append_near<4>(p, near, v, dv, a, b, q.s, acc);
@@ -507,6 +511,7 @@ __device__ __forceinline__ void split_apply_pass(const SsspParams &p, const Spli
     if (near) {
       a[0] = __ldg(p.off + v[0]);
       b[0] = __ldg(p.off + v[0] + 1);
+      checked_range(a[0], b[0], p.m, &p.hdr->status);
     }
     append_near<1>(p, near, v, dv, a, b, q.s, acc);
   }
@@ -569,7 +574,9 @@ __global__ void __launch_bounds__(1024) sssp_init(SsspParams p) {
     p.stamp[v] = kInf;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    p.fcur[0] = make_int4(p.source, 0, __ldg(p.off + p.source), __ldg(p.off + p.source + 1));
+    int a = __ldg(p.off + p.source), b = __ldg(p.off + p.source + 1);
+    checked_range(a, b, p.m, &p.hdr->status);
+    p.fcur[0] = make_int4(p.source, 0, a, b);
     WsHeader *h = p.hdr;
     h->aux[0] = 1ull;
     h->nf_split = p.delta ? p.delta : kNoSplit;

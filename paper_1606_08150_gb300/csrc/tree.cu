@@ -60,12 +60,14 @@ constexpr int kKidBatch = 8;
 __device__ __forceinline__ void load_kids(const TreeParams &p, int k0, int b, int (&c)[kKidBatch],
                                           int (&kc)[kKidBatch]) {
 #pragma unroll
-  for (int j = 0; j < kKidBatch; ++j) c[j] = k0 + j < b ? __ldg(p.cidx + k0 + j) : -1;
+  for (int j = 0; j < kKidBatch; ++j)
+    c[j] = k0 + j < b ? checked_index(__ldg(p.cidx + k0 + j), p.n, &p.hdr->status) : -1;
   int lo[kKidBatch], hi[kKidBatch];
 #pragma unroll
   for (int j = 0; j < kKidBatch; ++j) {
     lo[j] = c[j] >= 0 ? __ldg(p.coff + c[j]) : 0;
     hi[j] = c[j] >= 0 ? __ldg(p.coff + c[j] + 1) : 0;
+    checked_range(lo[j], hi[j], p.n - 1, &p.hdr->status);
   }
 #pragma unroll
   for (int j = 0; j < kKidBatch; ++j) kc[j] = hi[j] - lo[j];
@@ -98,7 +100,8 @@ __global__ void __launch_bounds__(1024) tree_post(TreeParams p, const int2 *__re
     for (int k0 = a; k0 < b; k0 += kKidBatch) {
       int c[kKidBatch], val[kKidBatch];
 #pragma unroll
-      for (int j = 0; j < kKidBatch; ++j) c[j] = k0 + j < b ? __ldg(p.cidx + k0 + j) : -1;
+      for (int j = 0; j < kKidBatch; ++j)
+        c[j] = k0 + j < b ? checked_index(__ldg(p.cidx + k0 + j), p.n, &p.hdr->status) : -1;
 #pragma unroll
       for (int j = 0; j < kKidBatch; ++j) val[j] = c[j] >= 0 ? __ldcg(p.out + c[j]) : 0;
 #pragma unroll
@@ -120,7 +123,9 @@ __global__ void __launch_bounds__(1024) tree_post_node(TreeParams p, int v) {
   const int a = __ldg(p.coff + v), b = __ldg(p.coff + v + 1);
   int acc = 0;
   for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
-    const int c = __ldcg(p.out + __ldg(p.cidx + k));
+    const int ci = checked_index(__ldg(p.cidx + k), p.n, &p.hdr->status);
+    if (kCheckedBuild && ci < 0) continue;
+    const int c = __ldcg(p.out + ci);
     acc = OP == kDescendants ? acc + 1 + c : max(acc, 1 + c);
   }
   if (OP == kDescendants) {
@@ -151,7 +156,8 @@ __global__ void __launch_bounds__(1024) tree_visit_node(TreeParams p, int v, int
   const int G = gridDim.x * blockDim.x;
   unsigned long long launched = 0, visited = 0;
   for (int k = a + blockIdx.x * blockDim.x + threadIdx.x; k < b; k += G) {
-    const int c = __ldg(p.cidx + k);
+    const int c = checked_index(__ldg(p.cidx + k), p.n, &p.hdr->status);
+    if (kCheckedBuild && c < 0) continue;
     p.out[c] = 0;
     visited++;
     const int kc = __ldg(p.coff + c + 1) - __ldg(p.coff + c);
@@ -413,11 +419,13 @@ __device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *uni
       const int k0 = a + j * kKidBatch;
       int c[kKidBatch], first[kKidBatch], kc[kKidBatch];
 #pragma unroll
-      for (int t = 0; t < kKidBatch; ++t) c[t] = k0 + t < b ? __ldg(p.cidx + k0 + t) : -1;
+      for (int t = 0; t < kKidBatch; ++t)
+        c[t] = k0 + t < b ? checked_index(__ldg(p.cidx + k0 + t), p.n, &p.hdr->status) : -1;
 #pragma unroll
       for (int t = 0; t < kKidBatch; ++t) {
         first[t] = c[t] >= 0 ? __ldg(p.coff + c[t]) : 0;
         kc[t] = c[t] >= 0 ? __ldg(p.coff + c[t] + 1) : 0;
+        checked_range(first[t], kc[t], p.n - 1, &p.hdr->status);
       }
       int mine = 0;
 #pragma unroll
@@ -517,7 +525,8 @@ __device__ __forceinline__ void queue_post_level(const TreeParams &p, const int4
     for (int k0 = a; k0 < b; k0 += kKidBatch) {
       int c[kKidBatch], val[kKidBatch];
 #pragma unroll
-      for (int t = 0; t < kKidBatch; ++t) c[t] = k0 + t < b ? __ldg(p.cidx + k0 + t) : -1;
+      for (int t = 0; t < kKidBatch; ++t)
+        c[t] = k0 + t < b ? checked_index(__ldg(p.cidx + k0 + t), p.n, &p.hdr->status) : -1;
 #pragma unroll
       for (int t = 0; t < kKidBatch; ++t) val[t] = c[t] >= 0 ? __ldcg(p.out + c[t]) : 0;
 #pragma unroll

@@ -76,7 +76,9 @@ class DpcError(RuntimeError):
 
 
 def _load_library() -> ctypes.CDLL:
-    path = _build.LIB
+    # DPC_LIBRARY=checked selects the bounds-checked build (built by
+    # build.build(checked=True)); the default is the regular build
+    path = _build.LIB_CHECKED if os.environ.get("DPC_LIBRARY") == "checked" else _build.LIB
     if not os.path.exists(path):
         raise ImportError(f"libdpc.so is not built ({path}); run __graft_entry__.build() or python -m "
                           "paper_1606_08150_gb300.build")
