@@ -140,6 +140,30 @@ def headline_workload(level, nrows, zipf_s):
             f"values N(0,1), x U[-1,1]")
 
 
+def gather_sectors(A, threshold=32, block_nnz=1 << 24):
+    """32-byte L2 sectors the SpMV kernels' x gathers touch: a warp request of
+    a long row's unit covers 32 consecutive non-zeros (adjacent lanes, the
+    row's first element at a request boundary), and touches one sector per
+    distinct col // 8 among them; a short row's thread gathers its non-zeros
+    one request each. Counted on the host, in blocks of rows."""
+    lens = np.diff(A.off).astype(np.int64)
+    total, r = 0, 0
+    while r < A.nrows:
+        hi = int(np.searchsorted(A.off, A.off[r] + block_nnz, side="right"))
+        hi = min(max(hi - 1, r + 1), A.nrows)
+        a, b = int(A.off[r]), int(A.off[hi])
+        sec = A.col[a:b].astype(np.int64) >> 3
+        ln = lens[r:hi]
+        pos = np.arange(b - a, dtype=np.int64) - np.repeat(A.off[r:hi].astype(np.int64) - a, ln)
+        new = np.ones(b - a, bool)
+        new[1:] = sec[1:] != sec[:-1]
+        new |= (pos % 32) == 0
+        is_long = np.repeat(ln > threshold, ln)
+        total += int(new[is_long].sum()) + int((~is_long).sum())
+        r = hi
+    return total
+
+
 def spmv_bytes(nrows, ncols, nnz):
     return 8 * nnz + 4 * (nrows + 1) + 4 * nrows + 4 * ncols
 
@@ -1076,6 +1100,29 @@ def main():
     achieved = bytes_ / (call_ms * 1e-3) / 1e9
     traffic, traffic_note = measured_traffic(bytes_, level)
 
+    # the ceiling of the SpMV's x gathers: random 4-byte loads from the same 4 MB x (held in L2), as many
+    # as the matrix has non-zeros, timed alone (dpc_gather_rate)
+    gather = None
+    if xd.numel() & (xd.numel() - 1) == 0:
+        gsum = torch.zeros(1, dtype=torch.float32, device="cuda")
+        props = torch.cuda.get_device_properties(0)
+        threads = props.multi_processor_count * 2048  # upper bound of the probe's resident threads
+        batches = max(1, -(-A.nnz // (threads * 16)))
+        gt = time_calls(lambda: dpc.gather_rate(xd, batches, gsum), 5, 2, stream)
+        n_g = dpc.gather_rate(xd, batches, gsum)
+        rate = n_g / (float(np.median(gt)) * 1e-3)
+        head_rate = A.nnz / (call_ms * 1e-3)
+        sectors = gather_sectors(A)
+        head_sectors = sectors / (call_ms * 1e-3)
+        gather = {"probe_gathers_per_s": round(rate / 1e9, 1), "unit": "G/s",
+                  "probe_l2_sector_GBps": round(rate * 32 / 1e9),
+                  "headline_gathers_per_s": round(head_rate / 1e9, 1),
+                  "headline_sectors_per_gather": round(sectors / A.nnz, 4),
+                  "headline_sectors_per_s": round(head_sectors / 1e9, 1),
+                  "headline_fraction_of_sector_rate": round(head_sectors / rate, 4),
+                  "probe": f"random 4-byte loads from x, {xd.numel():,} float32 ({xd.numel() * 4 / 2**20:.0f} MB, "
+                           f"held in L2), {n_g:,} loads, one sector each"}
+
     # ---- end to end through the public API with host (pinned) buffers
     h_off = torch.from_numpy(A.off).pin_memory()
     h_col = torch.from_numpy(A.col).pin_memory()
@@ -1144,6 +1191,7 @@ def main():
                      "peak_kind": peak_kind,
                      "kernel": KERNEL_OF_LEVEL.get(level, f"spmv_parent<{level}> and its children (one call)")},
         "cpu_baseline": cpu,
+        "l2_gather_ceiling": gather,
         "e2e": e2e,
         "gpu_launches": args.steps * (1 + int(stats0.child_launches)),
         "clocks": clk.summary(),

@@ -137,6 +137,20 @@ const char *dpc_status_string(dpc_status s);
  */
 dpc_status dpc_wait_selftest(uint32_t limit_us, uint32_t *status, dpc_stream_t stream);
 
+/*
+ * Diagnostic (no counterpart in the paper): the rate of random 4-byte gathers
+ * from an array held in L2, which bounds the SpMV kernels' gathers of x (one
+ * 32-byte L2 sector per 4 useful bytes when the columns are uniform). A grid
+ * of every resident block runs; each thread issues `batches` batches of 16
+ * independent loads x[i] at pseudo-random i in [0, n) through L2 and adds them
+ * into out[0] (so no load is dropped). n is a power of two from 32 to 2^26;
+ * x and out are device pointers. *gathers (host) receives the loads issued.
+ * Asynchronous on `stream`: time it with events there. Returns
+ * DPC_ERR_INVALID_ARG for bad sizes or null pointers.
+ */
+dpc_status dpc_gather_rate(const float *x, int32_t n, int32_t batches, float *out, int64_t *gathers,
+                           dpc_stream_t stream);
+
 /* Version of this ABI (bumped on incompatible change). */
 int32_t dpc_abi_version(void);
 

@@ -22,6 +22,11 @@ struct LaunchCfg {
   unsigned sub_delta;  // SSSP sub-split width for heavy vertices (0: none)
 };
 
+// Unit cursors of a consolidated loop: the units are split into kUnitCursors
+// partitions, each with a cursor on its own 128-byte line (kCursorStride words).
+constexpr int kUnitCursors = 8;
+constexpr int kCursorStride = 16;
+
 // Workspace header: counters that every call zeroes before its first kernel.
 // Counters that many warps update in the same phase, and the word that the
 // blocks of a grid barrier poll, sit on cache lines of their own: atomics on
@@ -50,8 +55,10 @@ struct WsHeader {
   unsigned nf_split_old;           // S before the split in progress
   unsigned nf_dmin;                // smallest distance at or above S (split in progress)
   unsigned nf_done;                // 1: a split found no vertex at or above S (the run is over)
+  // lines 8-15: the unit cursors of a consolidated loop (SpMV), one partition each
+  alignas(128) unsigned long long cursors[kUnitCursors * kCursorStride];
 };
-constexpr size_t kHeaderBytes = 1024;
+constexpr size_t kHeaderBytes = 2048;
 static_assert(sizeof(WsHeader) <= kHeaderBytes, "workspace header too large");
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

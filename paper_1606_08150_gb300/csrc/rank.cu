@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kRankPrepThreads) rank_prep_kernel(RankPrepPar
       q.hdr->cursor = 0;
       q.hdr->done_blocks2 = 0;
       q.hdr->launches = 0;
-      q.hdr->aux[2] = 0;  // the grid-level child's unit cursor
+      for (int c = 0; c < kUnitCursors; ++c) q.hdr->cursors[c * kCursorStride] = 0;  // the child's unit cursors
       if (q.stats) atomicMax(&q.stats->rounds, (unsigned)q.iteration + 1u);
       __threadfence();
     }

@@ -167,7 +167,7 @@ __device__ __forceinline__ void spmv_units_by_group(const SpmvParams &p, const i
   for (int u = lo + warp_in_group; u < hi; u += warps_in_group) spmv_unit<MODE>(p, units[u]);
 }
 
-// Units [0, n) handed to the calling warp from a shared cursor (zero before
+// Units [0, n) handed to the calling warp from shared cursors (zero before
 // the first warp starts). Row lengths vary, so a fixed warp-strided split ends
 // with most of the grid waiting on its slowest warps; on the 1M-row s = 1.5
 // matrix the cursor cut the unit phase by about 12 %. SpMV takes
@@ -176,18 +176,29 @@ __device__ __forceinline__ void spmv_units_by_group(const SpmvParams &p, const i
 // 3-8 % faster than one at a time for its 512-edge units.
 constexpr unsigned long long kRankGrab = 4;
 
+// The units are split into kUnitCursors equal partitions, each with its own
+// cursor on its own cache line (WsHeader::cursors): every atomic on one
+// address serialises in one L2 slice at about 2 ns, and with small units (the
+// mean-16 matrix: 35 K units of one row each) a single cursor made the unit
+// loop wait on its atomics. A warp starts on the partition of its index and,
+// once that one is exhausted, moves on to the next.
 template <int MODE>
 __device__ __forceinline__ void spmv_units_dynamic(const SpmvParams &p, const int4 *units, int n,
-                                                   unsigned long long *cursor) {
-  const unsigned long long grab =
-      MODE == kModeSpmv ? units_per_grab(n, (gridDim.x * blockDim.x) >> 5) : kRankGrab;
-  for (;;) {
-    unsigned long long i0 = 0;
-    if (lane_id() == 0) i0 = atomicAdd(cursor, grab);
-    i0 = __shfl_sync(0xffffffffu, i0, 0);
-    if (i0 >= (unsigned long long)n) break;
-    const int i1 = (int)min(i0 + grab, (unsigned long long)n);
-    for (int u = (int)i0; u < i1; ++u) spmv_unit<MODE>(p, units[u]);
+                                                   unsigned long long *cursors) {
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned long long grab = MODE == kModeSpmv ? units_per_grab(n, nw) : kRankGrab;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int t = 0; t < kUnitCursors; ++t) {
+    const int part = (w + t) % kUnitCursors;
+    const int lo = (int)((long long)n * part / kUnitCursors), hi = (int)((long long)n * (part + 1) / kUnitCursors);
+    for (;;) {
+      unsigned long long i0 = 0;
+      if (lane_id() == 0) i0 = atomicAdd(cursors + part * kCursorStride, grab);
+      i0 = __shfl_sync(0xffffffffu, i0, 0) + (unsigned long long)lo;
+      if (i0 >= (unsigned long long)hi) break;
+      const int i1 = (int)min(i0 + grab, (unsigned long long)hi);
+      for (int u = (int)i0; u < i1; ++u) spmv_unit<MODE>(p, units[u]);
+    }
   }
 }
 
@@ -392,7 +403,7 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
     if (grid_barrier_once(&p.hdr->done_blocks2)) {
       const int total = (int)min(*reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor),
                                  (unsigned long long)p.max_units);
-      spmv_units_dynamic<MODE>(p, p.units, total, &p.hdr->aux[2]);
+      spmv_units_dynamic<MODE>(p, p.units, total, p.hdr->cursors);
     } else if (threadIdx.x == 0) {
       spmv_fail(p, DPC_ERR_TIMEOUT);
     }
@@ -406,7 +417,7 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
         if (total > 0) {
           s_fail = 1;
           if (take_launch_slot(&p.hdr->launches, p.launch_budget)) {
-            s_fail = launch_consolidated_child<MODE>(p, p.units, total, &p.hdr->aux[2]) != cudaSuccess;
+            s_fail = launch_consolidated_child<MODE>(p, p.units, total, p.hdr->cursors) != cudaSuccess;
           }
           stat_add(p.stats, s_fail ? &dpc_stats::launch_failures : &dpc_stats::child_launches, 1);
         }

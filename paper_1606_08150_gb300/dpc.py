@@ -35,7 +35,7 @@ EXPORTS = (
     "dpc_bfs_rec_workspace_size", "dpc_bfs_rec",
     "dpc_graph_coloring_workspace_size", "dpc_graph_coloring",
     "dpc_engine_workspace_size", "dpc_engine_init", "dpc_engine_step",
-    "dpc_wait_selftest",
+    "dpc_wait_selftest", "dpc_gather_rate",
 )
 
 JOB_SSSP, JOB_TREE_DESCENDANTS, JOB_TREE_HEIGHT = 0, 1, 2
@@ -120,6 +120,8 @@ def _load_library() -> ctypes.CDLL:
     lib.dpc_engine_init.restype = st
     lib.dpc_engine_step.argtypes = [P, sz, i32, i32, i32, P, P, P, P, i32, P, P, P]
     lib.dpc_engine_step.restype = st
+    lib.dpc_gather_rate.argtypes = [P, i32, i32, P, P, P]
+    lib.dpc_gather_rate.restype = st
     lib.dpc_wait_selftest.argtypes = [ctypes.c_uint32, P, P]
     lib.dpc_wait_selftest.restype = st
     if hasattr(lib, "dpc_tree_height"):
@@ -234,6 +236,17 @@ def wait_selftest(limit_us: int, status: torch.Tensor, stream: Optional[torch.cu
         raise ValueError("status needs two elements")
     _check(_lib.dpc_wait_selftest(int(limit_us), _dptr(status, torch.int32, "status"), _stream(stream)),
            "dpc_wait_selftest")
+
+
+def gather_rate(x: torch.Tensor, batches: int, out: torch.Tensor,
+                stream: Optional[torch.cuda.Stream] = None) -> int:
+    """dpc_gather_rate: random 4-byte gathers from x (float32, a power-of-two
+    length) held in L2, summed into out[0]; returns the number of loads."""
+    g = ctypes.c_int64(0)
+    _check(_lib.dpc_gather_rate(_dptr(x, torch.float32, "x"), x.numel(), int(batches),
+                                _dptr(out, torch.float32, "out"), ctypes.byref(g), _stream(stream)),
+           "dpc_gather_rate")
+    return int(g.value)
 
 
 def spmv_csr_noalloc(off: torch.Tensor, col: torch.Tensor, val: torch.Tensor, x: torch.Tensor, y: torch.Tensor,

@@ -114,6 +114,15 @@ def test_host_only_calls(lib):
     assert lib.dpc_wait_selftest(ctypes.c_uint32(100), None, None) == 1
     assert lib.dpc_wait_selftest(ctypes.c_uint32(0), ctypes.byref(word), None) == 1
     assert lib.dpc_wait_selftest(ctypes.c_uint32(10_000_001), ctypes.byref(word), None) == 1
+    # the gather-rate diagnostic checks its sizes first (a power of two from 32 to 2^26)
+    g = ctypes.c_int64(0)
+    fake = ctypes.c_void_p(0x1000)
+    lib.dpc_gather_rate.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.dpc_gather_rate(fake, 1000, 1, fake, ctypes.byref(g), None) == 1
+    assert lib.dpc_gather_rate(fake, 1 << 27, 1, fake, ctypes.byref(g), None) == 1
+    assert lib.dpc_gather_rate(fake, 1 << 20, 0, fake, ctypes.byref(g), None) == 1
+    assert lib.dpc_gather_rate(None, 1 << 20, 1, fake, ctypes.byref(g), None) == 1
     for level in range(6):
         assert lib.dpc_pagerank_workspace_size(1000, 20000, level, None, ctypes.byref(out)) == 0
         assert out.value > 256 + 2 * 4000

@@ -27,3 +27,15 @@ def test_wait_runs_out_and_reports_timeout(dpc, limit_us):
     assert dpc.spmv_csr(dev(A.off), dev(A.col), dev(A.val), dev(x), y, "queue") == dpc.OK
     torch.cuda.synchronize()
     assert np.array_equal(y.cpu().numpy().astype(np.float64), oracle.spmv_f64(A.off, A.col, A.val, x)[0])
+
+
+def test_gather_rate_probe_counts_every_load(dpc):
+    """dpc_gather_rate (the ceiling of the SpMV gathers): over an array of ones
+    the sum it returns is the number of loads it reports, exactly (every
+    partial sum is an integer below 2^24)."""
+    x = torch.ones(1 << 20, dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    n = dpc.gather_rate(x, 1, out)
+    torch.cuda.synchronize()
+    assert n > 0 and n % 16 == 0 and n < (1 << 24)
+    assert float(out.item()) == float(n)
