@@ -282,7 +282,9 @@ def make_flush():
 
 # ---------------------------------------------------------------- secondary measurements
 
-def bench_spmv_levels(dpc, A, x, label, steps, flush, peak, levels, oracle_reps=0):
+def bench_spmv_levels(dpc, A, x, label, steps, flush, peak, levels, oracle_reps=0, autotune_levels=()):
+    """Every level with the default tuning; for each of autotune_levels also the
+    unit size (chunk) the autotuner picks for this matrix, timed the same way."""
     import torch
 
     off, col, val, xd = dev(A.off), dev(A.col), dev(A.val), dev(x)
@@ -302,6 +304,22 @@ def bench_spmv_levels(dpc, A, x, label, steps, flush, peak, levels, oracle_reps=
                       "GB/s": round(bytes_ / med / 1e6, 1), "frac_hbm": round(bytes_ / med / 1e6 / peak, 4),
                       "GFLOP/s": round(2 * A.nnz / med / 1e6, 1), "child_launches": stats.child_launches,
                       "launch_failures": stats.launch_failures, "status": stats.status}
+    for level in autotune_levels:
+        from paper_1606_08150_gb300 import autotune
+
+        chunks = (512, 1024, 2048, 4096)
+        ws = torch.empty(dpc.spmv_csr_workspace_size(A.nrows, A.nnz, level, dpc.Tuning(chunk=min(chunks))),
+                         dtype=torch.uint8, device="cuda")
+        run = lambda t: dpc.spmv_csr(off, col, val, xd, y, level, tuning=t, workspace=ws)
+        best, trials = autotune.search(run, autotune.grid_space(chunk=chunks), reps=5)
+        tun = dpc.Tuning(**best)
+        t = time_calls(lambda: run(tun), steps, 2, s, flush)
+        med = float(np.median(t))
+        res[level + "_autotuned"] = {"ms": round(med, 4), "ms_min": round(float(np.min(t)), 4),
+                                     "GB/s": round(bytes_ / med / 1e6, 1),
+                                     "frac_hbm": round(bytes_ / med / 1e6 / peak, 4), "tuning": best,
+                                     "search_ms_warm_l2": {tr.params["chunk"]: round(tr.ms, 4) for tr in trials}}
+        del ws
     out = {"workload": label, "nnz": A.nnz, "algorithmic_bytes": bytes_, "levels": res}
     if oracle_reps > 0:
         import oracle  # the CPU baseline: the oracle as it stands, one thread
@@ -774,7 +792,8 @@ def run_apps(dpc, levels, steps, peak, A=None, x=None):
     with_oracle = any(lv != "basic_dp" for lv in levels)  # the oracle is timed once, in the main process
     apps["spmv_zipf_mean16"] = bench_spmv_levels(dpc, A2, x, "1Mx1M zipf s=1.8795 (mean 16, nnz ~1.7e7)",
                                                  max(5, steps), flush, peak, levels,
-                                                 oracle_reps=3 if with_oracle else 0)
+                                                 oracle_reps=3 if with_oracle else 0,
+                                                 autotune_levels=[lv for lv in ("queue",) if lv in levels])
     del A2
     g12 = gen.rmat(12, seed=1)
     apps["sssp_rmat12"] = bench_sssp(dpc, g12, [0], "R-MAT scale 12, w in [1,100], source 0", 10, None, levels,
@@ -887,7 +906,7 @@ def merge_levels(apps, extra):
 
 # ---------------------------------------------------------------- per-level ncu ranges
 
-def profile_apps(dpc, only=None, levels=None, sssp_scale=18):
+def profile_apps(dpc, only=None, levels=None, sssp_scale=18, sssp_tuning=None):
     """One call of every application at every level, each inside its own
     cudaProfilerStart/Stop range (for `ncu --replay-mode range`, which sees the
     device-launched children that kernel replay cannot): warp execution
@@ -931,9 +950,10 @@ def profile_apps(dpc, only=None, levels=None, sssp_scale=18):
         off, col, w = dev(g.off), dev(g.col), dev(g.w)
         dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
         for level in levels:
-            ws = torch.empty(dpc.sssp_workspace_size(g.n, g.m, level), dtype=torch.uint8, device="cuda")
+            ws = torch.empty(dpc.sssp_workspace_size(g.n, g.m, level, sssp_tuning), dtype=torch.uint8, device="cuda")
             ranged(f"sssp_rmat{sssp_scale}", level,
-                   lambda st=None: dpc.sssp(off, col, w, 0, dist, level, workspace=ws, stats=st))
+                   lambda st=None: dpc.sssp(off, col, w, 0, dist, level, tuning=sssp_tuning, workspace=ws,
+                                            stats=st))
         del off, col, w, dist, ws
     if want("tree"):
         t = gen.tree(2_097_152, seed=4)
@@ -975,6 +995,40 @@ def profile_apps(dpc, only=None, levels=None, sssp_scale=18):
     return out
 
 
+def timing_suite(dpc):
+    """The calls --checked-overhead compares (median ms of 10 after 3 warm-ups,
+    L2 flushed before each): SSSP on R-MAT 18 (plain rounds and near-far), the
+    mean-16 SpMV, tree descendants on the 2M-node tree, all at the queue level."""
+    import torch
+
+    from paper_1606_08150_gb300 import gen
+
+    s = torch.cuda.current_stream()
+    flush = make_flush()
+    out = {}
+    g = gen.rmat(18, whi=1000, seed=2)
+    off, col, w = dev(g.off), dev(g.col), dev(g.w)
+    dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for name, tun in (("sssp_rmat18_queue", None), ("sssp_rmat18_queue_nearfar", dpc.Tuning(delta=200, sub_delta=8))):
+        ws = torch.empty(dpc.sssp_workspace_size(g.n, g.m, "queue", tun), dtype=torch.uint8, device="cuda")
+        out[name] = round(float(np.median(time_calls(
+            lambda: dpc.sssp(off, col, w, 0, dist, "queue", tuning=tun, workspace=ws), 10, 3, s, flush))), 4)
+    A = gen.zipf_csr(N_SPMV, N_SPMV, s=1.8795, lmax=200_000, seed=3)
+    x = gen.vector(N_SPMV, 3)
+    a_off, a_col, a_val, xd = dev(A.off), dev(A.col), dev(A.val), dev(x)
+    y = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+    ws = torch.empty(dpc.spmv_csr_workspace_size(A.nrows, A.nnz, "queue"), dtype=torch.uint8, device="cuda")
+    out["spmv_mean16_queue"] = round(float(np.median(time_calls(
+        lambda: dpc.spmv_csr(a_off, a_col, a_val, xd, y, "queue", workspace=ws), 10, 3, s, flush))), 4)
+    t = gen.tree(2_097_152, seed=4)
+    coff, cidx = dev(t.coff), dev(t.cidx)
+    o = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(dpc.tree_workspace_size(t.n, "queue"), dtype=torch.uint8, device="cuda")
+    out["tree_2m_queue"] = round(float(np.median(time_calls(
+        lambda: dpc.tree_descendants(coff, cidx, 0, o, "queue", workspace=ws), 10, 3, s, flush))), 4)
+    return out
+
+
 # ---------------------------------------------------------------- main arm
 
 def main():
@@ -1002,6 +1056,11 @@ def main():
                     help="with --profile-apps: comma-separated application prefixes (spmv,sssp,tree,pagerank,bfs,graph)")
     ap.add_argument("--profile-sssp-scale", type=int, default=18,
                     help="with --profile-apps: R-MAT scale of the SSSP graph (w in [1,1000], source 0)")
+    ap.add_argument("--profile-sssp-tuning", default=None,
+                    help="with --profile-apps: near-far split and sub-split widths for SSSP, e.g. 200,8")
+    ap.add_argument("--checked-overhead", action="store_true",
+                    help="time a few calls with the regular and the bounds-checked library and print both")
+    ap.add_argument("--timing-suite", action="store_true", help="internal: the calls --checked-overhead times")
     ap.add_argument("--profile-levels", default=None,
                     help="with --profile-apps: comma-separated levels (basic-DP gets a large launch pool, the others "
                          "the library default)")
@@ -1030,8 +1089,33 @@ def main():
         # basic-DP needs room for one launch per large item; the other levels run with the
         # library's small default pool (launch latency grows with the pool)
         _dpc.device_init(local, BASIC_DP_POOL if plevels is None or "basic_dp" in plevels else 0)
+        tun = None
+        if args.profile_sssp_tuning:
+            dlt, sub = (int(v) for v in args.profile_sssp_tuning.split(","))
+            tun = _dpc.Tuning(delta=dlt, sub_delta=sub)
         profile_apps(_dpc, args.profile_only.split(",") if args.profile_only else None, plevels,
-                     args.profile_sssp_scale)
+                     args.profile_sssp_scale, tun)
+        return
+    if args.timing_suite:
+        from paper_1606_08150_gb300 import dpc as _dpc
+
+        _dpc.device_init(local, 0)
+        print(json.dumps(timing_suite(_dpc)))
+        return
+    if args.checked_overhead:
+        from paper_1606_08150_gb300 import build as _b
+
+        _b.build(checked=True)
+        runs = {}
+        for name, env in (("regular", {}), ("checked", {"DPC_LIBRARY": "checked"})):
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--timing-suite"], capture_output=True,
+                                 text=True, env=dict(os.environ, **env), timeout=1200)
+            if out.returncode != 0:
+                raise RuntimeError(out.stderr[-2000:])
+            runs[name] = json.loads(out.stdout.strip().splitlines()[-1])
+        print(json.dumps({"checked_overhead": {k: {"regular_ms": runs["regular"][k], "checked_ms": runs["checked"][k],
+                                                   "ratio": round(runs["checked"][k] / runs["regular"][k], 3)}
+                                               for k in runs["regular"]}}))
         return
     if args.serve_only:
         from paper_1606_08150_gb300 import dpc as _dpc

@@ -154,7 +154,7 @@ class Cache:
 def default_space(app: str, level: str) -> List[Dict[str, int]]:
     """Search space per application and level (threshold, chunk, child shape)."""
     if app == "spmv":
-        return grid_space(chunk=(1024, 2048, 4096, 8192), child_threads=(128, 256, 512),
+        return grid_space(chunk=(512, 1024, 2048, 4096, 8192), child_threads=(128, 256, 512),
                           kc=(KC_RULE.get(level, 1), max(1, KC_RULE.get(level, 1) // 4)))
     if app == "sssp":
         return grid_space(threshold=(16, 32, 64), chunk=(128, 256, 1024), kc=(KC_RULE.get(level, 1),))

@@ -188,20 +188,26 @@ __device__ __forceinline__ bool last_block_done(unsigned *counter) {
   return s_last != 0u;
 }
 
-// Blocking grid-wide barrier for a cooperative launch (every block resident),
+// One-shot grid-wide barrier for a cooperative launch (every block resident),
 // used once per call: `counter` must be zero when the grid starts. Each block
-// arrives after making its writes visible and waits until all have arrived.
-// The wait is bounded (WaitClock); when it runs out the function returns
-// false in that block and the caller reports DPC_ERR_TIMEOUT instead of
-// hanging. Must be called by all threads of a block.
-
-__device__ __forceinline__ bool grid_barrier_once(unsigned *counter) {
-  __shared__ int s_ok;
+// arrives after making its writes visible (grid_arrive) and waits until all
+// have arrived (grid_wait_all); work that needs nothing from the other blocks
+// may run between the two halves. The wait is bounded (WaitClock); when it
+// runs out grid_wait_all returns false in that block and the caller reports
+// DPC_ERR_TIMEOUT instead of hanging. Both halves must be called by all
+// threads of a block.
+__device__ __forceinline__ void grid_arrive(unsigned *counter) {
   __syncthreads();  // orders the block's writes before its master thread's fence and arrival
   if (threadIdx.x == 0) {
     __threadfence();
-    int ok = 1;
     atomicAdd(counter, 1u);
+  }
+}
+
+__device__ __forceinline__ bool grid_wait_all(unsigned *counter) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
     WaitClock clk;
     while (*reinterpret_cast<volatile unsigned *>(counter) < gridDim.x) {
       __nanosleep(64);

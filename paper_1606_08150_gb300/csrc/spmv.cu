@@ -22,7 +22,9 @@
 // non-zero row is spread over the whole child grid instead of one block. A row
 // split into several units is finished by whichever warp completes its last
 // unit, which adds the unit partial sums in unit order: every level sums each
-// row in a fixed order, so results are bitwise reproducible run to run.
+// row in a fixed order, so results are bitwise reproducible run to run. A unit
+// carries its own range of non-zeros, (row, first non-zero, end of the row,
+// first unit of the row), so processing it needs no row-offset lookup.
 //
 // The same kernels serve PageRank's pull step (rank.cu) in a second mode: a
 // row is a vertex, its entries are the vertex's in-edges, every term is the
@@ -125,24 +127,25 @@ __device__ __forceinline__ float group_dot(const SpmvParams &p, int a, int b, in
   return acc;
 }
 
-// One work unit (row, k, units_of_row, first_unit) processed by a full warp.
+// The end of unit u's sum s (already reduced over the warp): the row's result
+// when the unit is the row's only one, else its partial sum, and the row's
+// result from the warp that completes the row's last unit. Unit u of the
+// buffer, e = (row, a, row_end, first), holds the non-zeros [a, b), b =
+// min(a + chunk, row_end); the row's units are first, first + 1, ..., the last
+// one reaching row_end, so the row has (u - first) + ceil((row_end - a) /
+// chunk) of them.
 template <int MODE>
-__device__ __forceinline__ void spmv_unit(const SpmvParams &p, int4 u) {
+__device__ __forceinline__ void unit_finish(const SpmvParams &p, int u, int4 e, int b, float s) {
   const int lane = lane_id();
-  const int row = u.x, k = u.y, nun = u.z, first = u.w;
-  if (row < 0) return;  // placeholder written after a buffer overflow
-  int r0 = __ldg(p.off + row), r1 = __ldg(p.off + row + 1);
-  checked_range(r0, r1, p.nnz, &p.hdr->status);
-  const int a = r0 + k * p.chunk;
-  const int b = min(r1, a + p.chunk);
-  float s = warp_sum(group_dot<MODE>(p, a, b, lane, kWarp));
-  if (nun == 1) {
+  const int row = e.x, a = e.y, row_end = e.z, first = e.w;
+  if (u == first && b == row_end) {  // the row's only unit
     if (lane == 0) p.y[row] = row_result<MODE>(p, s);
     return;
   }
+  const int nun = (u - first) + ceil_div(row_end - a, p.chunk);
   unsigned last = 0;
   if (lane == 0) {
-    p.partial[first + k] = s;
+    p.partial[u] = s;
     __threadfence();
     last = (atomicAdd(p.ucount + first, 1u) == (unsigned)(nun - 1)) ? 1u : 0u;
   }
@@ -160,11 +163,19 @@ __device__ __forceinline__ void spmv_unit(const SpmvParams &p, int4 u) {
   }
 }
 
+// Unit u processed by a full warp.
+template <int MODE>
+__device__ __forceinline__ void spmv_unit(const SpmvParams &p, int u, int4 e) {
+  if (e.x < 0) return;  // placeholder written after a buffer overflow
+  const int b = min(e.z, e.y + p.chunk);
+  unit_finish<MODE>(p, u, e, b, warp_sum(group_dot<MODE>(p, e.y, b, lane_id(), kWarp)));
+}
+
 // Units [lo, hi) processed by the warps of the calling group, warp-strided.
 template <int MODE>
 __device__ __forceinline__ void spmv_units_by_group(const SpmvParams &p, const int4 *units, int lo, int hi,
                                                     int warp_in_group, int warps_in_group) {
-  for (int u = lo + warp_in_group; u < hi; u += warps_in_group) spmv_unit<MODE>(p, units[u]);
+  for (int u = lo + warp_in_group; u < hi; u += warps_in_group) spmv_unit<MODE>(p, u, __ldcg(units + u));
 }
 
 // Units [0, n) handed to the calling warp from shared cursors (zero before
@@ -181,10 +192,19 @@ constexpr unsigned long long kRankGrab = 4;
 // address serialises in one L2 slice at about 2 ns, and with small units (the
 // mean-16 matrix: 35 K units of one row each) a single cursor made the unit
 // loop wait on its atomics. A warp starts on the partition of its index and,
-// once that one is exhausted, moves on to the next.
+// once that one is exhausted, moves on to the next; every grab that lands
+// inside the partition is processed by the warp that made it.
+//
+// The device-launched child (grid level) grabs when it needs a unit. The
+// queue level, whose warps all start together, keeps its next grab in flight
+// and loads the next unit while it processes the current one, so that
+// neither round trip sits between two units. (In the child, whose blocks
+// start while the parent still holds the GPU, grabbing ahead let the first
+// warps reserve units that later ones would have taken: the grid level lost
+// 2-5 %.)
 template <int MODE>
-__device__ __forceinline__ void spmv_units_dynamic(const SpmvParams &p, const int4 *units, int n,
-                                                   unsigned long long *cursors) {
+__device__ __forceinline__ void spmv_units_on_demand(const SpmvParams &p, const int4 *units, int n,
+                                                     unsigned long long *cursors) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const unsigned long long grab = MODE == kModeSpmv ? units_per_grab(n, nw) : kRankGrab;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -197,7 +217,48 @@ __device__ __forceinline__ void spmv_units_dynamic(const SpmvParams &p, const in
       i0 = __shfl_sync(0xffffffffu, i0, 0) + (unsigned long long)lo;
       if (i0 >= (unsigned long long)hi) break;
       const int i1 = (int)min(i0 + grab, (unsigned long long)hi);
-      for (int u = (int)i0; u < i1; ++u) spmv_unit<MODE>(p, units[u]);
+      for (int u = (int)i0; u < i1; ++u) spmv_unit<MODE>(p, u, __ldcg(units + u));
+    }
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void spmv_units_dynamic(const SpmvParams &p, const int4 *units, int n,
+                                                   unsigned long long *cursors) {
+  const int lane = lane_id();
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned long long grab = MODE == kModeSpmv ? units_per_grab(n, nw) : kRankGrab;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int t = 0; t < kUnitCursors; ++t) {
+    const int part = (w + t) % kUnitCursors;
+    const int lo = (int)((long long)n * part / kUnitCursors), hi = (int)((long long)n * (part + 1) / kUnitCursors);
+    unsigned long long *cur = cursors + part * kCursorStride;
+    unsigned long long g = 0;
+    if (lane == 0) g = atomicAdd(cur, grab);
+    g = __shfl_sync(0xffffffffu, g, 0) + (unsigned long long)lo;
+    if (g >= (unsigned long long)hi) continue;
+    int u = (int)g, uend = (int)min(g + grab, (unsigned long long)hi);
+    int4 e = __ldcg(units + u);
+    unsigned long long gn = 0;  // the next grab (lane 0), in flight
+    if (lane == 0) gn = atomicAdd(cur, grab);
+    for (;;) {
+      int un = u + 1, unend = uend;
+      if (un >= uend) {
+        const unsigned long long g2 = __shfl_sync(0xffffffffu, gn, 0) + (unsigned long long)lo;
+        if (g2 < (unsigned long long)hi) {
+          un = (int)g2;
+          unend = (int)min(g2 + grab, (unsigned long long)hi);
+          if (lane == 0) gn = atomicAdd(cur, grab);
+        } else {
+          un = -1;
+        }
+      }
+      const int4 en = un >= 0 ? __ldcg(units + un) : make_int4(-1, 0, 0, 0);
+      spmv_unit<MODE>(p, u, e);
+      if (un < 0) break;
+      u = un;
+      uend = unend;
+      e = en;
     }
   }
 }
@@ -206,27 +267,28 @@ __device__ __forceinline__ void spmv_units_dynamic(const SpmvParams &p, const in
 
 // ------------------------------------------------------------------ kernels
 
-// Consolidated child (moldable): every warp takes units until the buffer is
-// exhausted, whatever the grid size (Sec. IV.C) - from a shared cursor when the
-// child is the only one of its call (grid level), else round-robin.
+// Consolidated child (moldable): every warp takes units of the buffer
+// [lo, lo + n) until they are exhausted, whatever the grid size (Sec. IV.C) -
+// from shared cursors when the child is the only one of its call (grid level,
+// lo = 0), else round-robin. Unit indices are slots of the whole buffer
+// (p.units), the numbering the units' first-unit fields use.
 template <int MODE>
-__global__ void __launch_bounds__(1024) spmv_child(SpmvParams p, const int4 *__restrict__ units, int nunits,
-                                                  unsigned long long *cursor) {
+__global__ void __launch_bounds__(1024) spmv_child(SpmvParams p, int lo, int n, unsigned long long *cursor) {
   if (cursor) {
-    spmv_units_dynamic<MODE>(p, units, nunits, cursor);
+    spmv_units_on_demand<MODE>(p, p.units, n, cursor);
     return;
   }
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  spmv_units_by_group<MODE>(p, units, 0, nunits, gw, nw);
+  spmv_units_by_group<MODE>(p, p.units, lo, lo + n, gw, nw);
 }
 
-// Launch the consolidated child for units [0, n) of `units` from the device.
+// Launch the consolidated child for units [lo, lo + n) of the buffer from the device.
 template <int MODE>
-__device__ __forceinline__ cudaError_t launch_consolidated_child(const SpmvParams &p, const int4 *units, int n,
+__device__ __forceinline__ cudaError_t launch_consolidated_child(const SpmvParams &p, int lo, int n,
                                                                  unsigned long long *cursor = nullptr) {
   spmv_child<MODE><<<child_grid_for(n, p.child_blocks, p.child_threads), p.child_threads, 0, cudaStreamFireAndForget>>>(
-      p, units, n, cursor);
+      p, lo, n, cursor);
   return cudaGetLastError();
 }
 
@@ -293,35 +355,102 @@ __global__ void __launch_bounds__(1024) spmv_basic_parent(SpmvParams p) {
   }
 }
 
+// Rows a parent thread keeps in registers between its passes: rows t, t + G,
+// ..., up to kRowRegs of them (t the thread's index in the grid, G the grid's
+// thread count), as (first non-zero, length). With more rows per thread the
+// passes load the offsets again.
+constexpr int kRowRegs = 8;
+
+// The long row at (start a, length len) of row r into the buffer from unit
+// slot pos on: its ceil(len / chunk) units. Returns the slot after them.
+template <int MODE>
+__device__ __forceinline__ int write_row_units(const SpmvParams &p, int r, int a, int len, int pos) {
+  const int nu = ceil_div(len, p.chunk);
+  for (int k = 0; k < nu; ++k) p.units[pos + k] = make_int4(r, a + k * p.chunk, a + len, pos);
+  p.ucount[pos] = 0u;
+  return pos + nu;
+}
+
+// The short rows of this thread computed inline (rows handed to the buffer
+// skipped while the group's buffer holds them, `buffered`): from the
+// registers of pass 1 (regs), else with the offsets loaded again. (Summing
+// four rows side by side in steps of two terms, to keep more loads in flight,
+// was slower: a warp's loop then runs until the longest of 128 rows is done.)
+template <int MODE>
+__device__ __forceinline__ unsigned long long spmv_short_rows(const SpmvParams &p, bool regs, const int *ra,
+                                                               const int *rl, int t0, int G, bool buffered) {
+  unsigned long long inl = 0;
+  if (regs) {
+#pragma unroll
+    for (int j = 0; j < kRowRegs; ++j) {
+      if (rl[j] < 0 || (buffered && rl[j] > p.threshold)) continue;
+      p.y[t0 + j * G] = row_result<MODE>(p, seq_dot<MODE>(p, ra[j], ra[j] + rl[j]));
+      inl++;
+    }
+  } else {
+    for (int r = t0; r < p.nrows; r += G) {
+      const int a = __ldg(p.off + r), b = __ldg(p.off + r + 1);
+      if (buffered && b - a > p.threshold) continue;  // handed to the child
+      p.y[r] = row_result<MODE>(p, seq_dot<MODE>(p, a, b));
+      inl++;
+    }
+  }
+  return inl;
+}
+
 // Warp-, block-, grid- and queue-level consolidated parent (Fig. 4b). The first pass
-// counts the units of the thread's long rows so that the warp (block) reserves
-// its whole buffer with one atomic - the exact per-buffer size that the
-// paper's perBufferSize rule estimates (Sec. IV.E); the second writes the long
-// rows' units into the reserved slice, each thread at the offset given by a
-// warp (block) scan; then the scope's barrier and the launch; the third pass
-// computes the short rows inline while the child already runs (the paper's
-// postwork position, Fig. 4b, holds no work here).
+// loads the thread's row offsets and counts the units of its long rows, so
+// that the warp (block) reserves its whole buffer with one atomic - the exact
+// per-buffer size that the paper's perBufferSize rule estimates (Sec. IV.E);
+// each thread then writes its long rows' units into its own stretch of the
+// reserved slice, at the offset given by a warp (block) scan; then the
+// scope's barrier and the launch; the third pass computes the short rows
+// inline while the child already runs (the paper's postwork position, Fig.
+// 4b, holds no work here). The queue level arrives at its grid barrier, does
+// its short rows and only then waits, so the barrier's latency and the
+// blocks' uneven arrival hide behind that work.
 template <int LEVEL, int MODE>
 __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
   __shared__ int s_scan[33];
   __shared__ int s_base, s_fail;
   const int lane = lane_id();
   const int G = gridDim.x * blockDim.x;
-  const int bstart = blockIdx.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool regs = (long long)p.nrows <= (long long)kRowRegs * G;
 
-  // pass 1: units owned by this thread
+  // pass 1: the thread's rows and the units of its long ones
+  int ra[kRowRegs], rl[kRowRegs];
   int mine = 0;
-  for (int r = bstart + threadIdx.x; r < p.nrows; r += G) {
-    const int len = __ldg(p.off + r + 1) - __ldg(p.off + r);
-    if (len > p.threshold) mine += ceil_div(len, p.chunk);
+  if (regs) {
+#pragma unroll
+    for (int j = 0; j < kRowRegs; ++j) {
+      ra[j] = 0;
+      rl[j] = -1;
+      const long long r = (long long)t0 + (long long)j * G;
+      if (r < p.nrows) {
+        int a = __ldg(p.off + r), b = __ldg(p.off + r + 1);
+        checked_range(a, b, p.nnz, &p.hdr->status);
+        ra[j] = a;
+        rl[j] = b - a;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kRowRegs; ++j)
+      if (rl[j] > p.threshold) mine += ceil_div(rl[j], p.chunk);
+  } else {
+    for (int r = t0; r < p.nrows; r += G) {
+      const int len = __ldg(p.off + r + 1) - __ldg(p.off + r);
+      if (len > p.threshold) mine += ceil_div(len, p.chunk);
+    }
   }
-  // reserve the group's slice of the unit list
-  int base, gtotal;
+  // reserve the group's slice of the unit list; the thread's stretch starts at pos
+  int base, gtotal, pos;
   if (LEVEL == DPC_BLOCK || LEVEL == DPC_QUEUE) {
-    gtotal = block_sum(mine, s_scan);
+    const int excl = block_exclusive_scan(mine, s_scan, &gtotal);
     if (threadIdx.x == 0) s_base = gtotal ? (int)atomicAdd(&p.hdr->cursor, (unsigned long long)gtotal) : 0;
     __syncthreads();
     base = s_base;
+    pos = base + excl;
     if (base + gtotal > p.max_units) {  // only reachable with malformed offsets
       if (threadIdx.x == 0) spmv_fail(p, DPC_ERR_OVERFLOW);
       for (int j = base + threadIdx.x; j < min(base + gtotal, p.max_units); j += blockDim.x)
@@ -329,10 +458,12 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
       gtotal = 0;
     }
   } else {
-    gtotal = warp_sum(mine);
+    const int inc = warp_inclusive_scan(mine);
+    gtotal = __shfl_sync(0xffffffffu, inc, kWarp - 1);
     int b0 = 0;
     if (lane == 0 && gtotal) b0 = (int)atomicAdd(&p.hdr->cursor, (unsigned long long)gtotal);
     base = __shfl_sync(0xffffffffu, b0, 0);
+    pos = base + inc - mine;
     if (base + gtotal > p.max_units) {  // only reachable with malformed offsets
       if (lane == 0) spmv_fail(p, DPC_ERR_OVERFLOW);
       for (int j = base + lane; j < min(base + gtotal, p.max_units); j += kWarp) p.units[j] = make_int4(-1, 0, 1, 0);
@@ -341,33 +472,28 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
   }
 
   // pass 2: long rows into the buffer
-  int run = base;
   unsigned long long buf = 0;
-  for (int r0 = bstart; r0 < p.nrows; r0 += G) {
-    const int r = r0 + threadIdx.x;
-    int nu = 0;
-    if (r < p.nrows && gtotal) {
-      const int len = __ldg(p.off + r + 1) - __ldg(p.off + r);
-      if (len > p.threshold) nu = ceil_div(len, p.chunk);
-    }
-    int excl, step;
-    if (LEVEL == DPC_BLOCK || LEVEL == DPC_QUEUE) {
-      excl = block_exclusive_scan(nu, s_scan, &step);
+  if (gtotal) {
+    if (regs) {
+#pragma unroll
+      for (int j = 0; j < kRowRegs; ++j) {
+        if (rl[j] <= p.threshold) continue;
+        pos = write_row_units<MODE>(p, t0 + j * G, ra[j], rl[j], pos);
+        buf++;
+      }
     } else {
-      const int inc = warp_inclusive_scan(nu);
-      excl = inc - nu;
-      step = __shfl_sync(0xffffffffu, inc, kWarp - 1);
+      for (int r = t0; r < p.nrows; r += G) {
+        int a = __ldg(p.off + r), b = __ldg(p.off + r + 1);
+        checked_range(a, b, p.nnz, &p.hdr->status);
+        if (b - a <= p.threshold) continue;
+        pos = write_row_units<MODE>(p, r, a, b - a, pos);
+        buf++;
+      }
     }
-    if (nu) {
-      const int pos = run + excl;
-      for (int k = 0; k < nu; ++k) p.units[pos + k] = make_int4(r, k, nu, pos);
-      p.ucount[pos] = 0u;
-      buf++;
-    }
-    run += step;
   }
 
   // barrier of the consolidation scope, then one selected thread launches
+  unsigned long long inl = 0;
   if (LEVEL == DPC_WARP) {
     __threadfence();
     __syncwarp();
@@ -376,7 +502,7 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
       if (lane == 0) {
         failed = 1;
         if (take_launch_slot(&p.hdr->launches, p.launch_budget)) {
-          failed = launch_consolidated_child<MODE>(p, p.units + base, gtotal) != cudaSuccess;
+          failed = launch_consolidated_child<MODE>(p, base, gtotal) != cudaSuccess;
         }
         stat_add(p.stats, failed ? &dpc_stats::launch_failures : &dpc_stats::child_launches, 1);
       }
@@ -390,7 +516,7 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
       if (threadIdx.x == 0) {
         s_fail = 1;
         if (take_launch_slot(&p.hdr->launches, p.launch_budget)) {
-          s_fail = launch_consolidated_child<MODE>(p, p.units + base, gtotal) != cudaSuccess;
+          s_fail = launch_consolidated_child<MODE>(p, base, gtotal) != cudaSuccess;
         }
         stat_add(p.stats, s_fail ? &dpc_stats::launch_failures : &dpc_stats::child_launches, 1);
       }
@@ -400,7 +526,9 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
   } else if (LEVEL == DPC_QUEUE) {
     // every block has buffered its long rows once all have arrived; then the
     // whole grid runs the consolidated child's loop over the buffer
-    if (grid_barrier_once(&p.hdr->done_blocks2)) {
+    grid_arrive(&p.hdr->done_blocks2);
+    inl = spmv_short_rows<MODE>(p, regs, ra, rl, t0, G, gtotal != 0);
+    if (grid_wait_all(&p.hdr->done_blocks2)) {
       const int total = (int)min(*reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor),
                                  (unsigned long long)p.max_units);
       spmv_units_dynamic<MODE>(p, p.units, total, p.hdr->cursors);
@@ -417,7 +545,7 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
         if (total > 0) {
           s_fail = 1;
           if (take_launch_slot(&p.hdr->launches, p.launch_budget)) {
-            s_fail = launch_consolidated_child<MODE>(p, p.units, total, p.hdr->cursors) != cudaSuccess;
+            s_fail = launch_consolidated_child<MODE>(p, 0, total, p.hdr->cursors) != cudaSuccess;
           }
           stat_add(p.stats, s_fail ? &dpc_stats::launch_failures : &dpc_stats::child_launches, 1);
         }
@@ -428,14 +556,10 @@ __global__ void __launch_bounds__(1024) spmv_parent(SpmvParams p) {
   }
 
   // pass 3: short rows inline. This comes after the launch so that the
-  // consolidated child runs while the parent threads finish their own rows.
-  unsigned long long inl = 0;
-  for (int r = bstart + threadIdx.x; r < p.nrows; r += G) {
-    const int a = __ldg(p.off + r), b = __ldg(p.off + r + 1);
-    if (gtotal && b - a > p.threshold) continue;  // handed to the child
-    p.y[r] = row_result<MODE>(p, seq_dot<MODE>(p, a, b));
-    inl++;
-  }
+  // consolidated child runs while the parent threads finish their own rows
+  // (the queue level did them between the halves of its barrier). The offsets
+  // are loaded again: kept in registers across the device launch, they spilled.
+  if (LEVEL != DPC_QUEUE) inl = spmv_short_rows<MODE>(p, false, ra, rl, t0, G, gtotal != 0);
   if (p.stats) {
     inl = warp_sum(inl);
     buf = warp_sum(buf);
@@ -492,17 +616,18 @@ __global__ void __launch_bounds__(1024) rank_queue_kernel(RankQueueArgs a) {
   unsigned long long buffered = 0, inl = 0;
   for (int r0i = bstart; r0i < p.nrows; r0i += G) {
     const int r = r0i + threadIdx.x;
-    int nu = 0;
+    int nu = 0, ra = 0, len = 0;
     if (r < p.nrows && gtotal) {
-      const int len = __ldg(p.off + r + 1) - __ldg(p.off + r);
+      int rb = __ldg(p.off + r + 1);
+      ra = __ldg(p.off + r);
+      checked_range(ra, rb, p.nnz, &p.hdr->status);
+      len = rb - ra;
       if (len > p.threshold) nu = ceil_div(len, p.chunk);
     }
     int step;
     const int excl = block_exclusive_scan(nu, s_scan, &step);
     if (nu) {
-      const int pos = run + excl;
-      for (int k = 0; k < nu; ++k) p.units[pos + k] = make_int4(r, k, nu, pos);
-      p.ucount[pos] = 0u;
+      write_row_units<kModeRank>(p, r, ra, len, run + excl);
       buffered++;
     } else if (r < p.nrows) {
       inl++;
@@ -547,7 +672,7 @@ __global__ void __launch_bounds__(1024) rank_queue_kernel(RankQueueArgs a) {
       i0 = __shfl_sync(0xffffffffu, i0, 0);
       if (i0 >= (unsigned long long)total) break;
       const int i1 = (int)min(i0 + grab, (unsigned long long)total);
-      for (int u = (int)i0; u < i1; ++u) spmv_unit<kModeRank>(p, __ldcg(p.units + u));
+      for (int u = (int)i0; u < i1; ++u) spmv_unit<kModeRank>(p, u, __ldcg(p.units + u));
     }
     for (int r = bstart + threadIdx.x; r < p.nrows; r += G) {
       const int aa = __ldg(p.off + r), bb = __ldg(p.off + r + 1);

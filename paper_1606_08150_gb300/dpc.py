@@ -77,8 +77,10 @@ class DpcError(RuntimeError):
 
 def _load_library() -> ctypes.CDLL:
     # DPC_LIBRARY=checked selects the bounds-checked build (built by
-    # build.build(checked=True)); the default is the regular build
-    path = _build.LIB_CHECKED if os.environ.get("DPC_LIBRARY") == "checked" else _build.LIB
+    # build.build(checked=True)), DPC_LIBRARY=<file>.so another build of the
+    # library (to compare two builds); the default is the regular build
+    sel = os.environ.get("DPC_LIBRARY", "")
+    path = _build.LIB_CHECKED if sel == "checked" else (sel if sel.endswith(".so") else _build.LIB)
     if not os.path.exists(path):
         raise ImportError(f"libdpc.so is not built ({path}); run __graft_entry__.build() or python -m "
                           "paper_1606_08150_gb300.build")
