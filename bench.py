@@ -657,25 +657,37 @@ def bench_serve(count=4096, rate=2000.0, seed=5):
         srv.run(reqs[:64])  # warm-up (graph capture, module load)
         srv.reset()
         eng = srv.run(reqs)
+        del srv
+        torch_empty_cache()
+        rsrv = serve.ResidentServer(graphs, trees)
+        rsrv.run(reqs[:64])
+        rsrv.reset()
+        res_eng = rsrv.run(reqs)
+        del rsrv
+        torch_empty_cache()
         base = serve.one_at_a_time(graphs, trees, reqs)
-        le, lb = eng.latencies(arr) * 1e3, base.latencies(arr) * 1e3
+        le, lb, lr = eng.latencies(arr) * 1e3, base.latencies(arr) * 1e3, res_eng.latencies(arr) * 1e3
         res[label] = {
             "engine": {"req_per_s": round(count / eng.makespan, 1), "p50_ms": round(float(np.percentile(le, 50)), 3),
                        "p99_ms": round(float(np.percentile(le, 99)), 3), "slots": eng.slots, "steps": eng.steps,
                        "status": eng.status},
+            "resident": {"req_per_s": round(count / res_eng.makespan, 1),
+                         "p50_ms": round(float(np.percentile(lr, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lr, 99)), 3), "slots": res_eng.slots,
+                         "kernel_launches": res_eng.steps, "status": res_eng.status},
             "one_at_a_time": {"req_per_s": round(count / base.makespan, 1),
                               "p50_ms": round(float(np.percentile(lb, 50)), 3),
                               "p99_ms": round(float(np.percentile(lb, 99)), 3)},
             "throughput_ratio": round(base.makespan / eng.makespan, 3),
+            "resident_throughput_ratio": round(base.makespan / res_eng.makespan, 3),
         }
-        del srv
-        torch_empty_cache()
     # capacity at a stated tail latency: the engine under rising offered load
     # (one request stream per rate), against one-at-a-time's saturated throughput,
     # with the engine's default configuration and with the tuned one
     base_cap = res["saturated"]["one_at_a_time"]["req_per_s"]
     for name, make in (("default", lambda: serve.Server(graphs, trees, waves_per_step=32)),
-                       ("tuned", lambda: serve.server_from_cache(cache, graphs, trees))):
+                       ("tuned", lambda: serve.server_from_cache(cache, graphs, trees)),
+                       ("resident", lambda: serve.ResidentServer(graphs, trees))):
         sweep, best = [], None
         for r in (2000.0, 4000.0, 8000.0, 10000.0, 12000.0, 14000.0, 16000.0, 32000.0):
             reqs = serve.poisson_stream(np.random.default_rng(seed + 2), count, r, len(graphs), len(trees), sources)
@@ -693,14 +705,52 @@ def bench_serve(count=4096, rate=2000.0, seed=5):
                 best = row
             del srv
             torch_empty_cache()
-        key = "" if name == "default" else "_tuned"
+        key = "" if name == "default" else "_" + name
         res["load_sweep" + key] = sweep
         res["capacity" + key] = {"p99_bound_ms": SERVE_P99_MS,
                                  "engine_req_per_s": best["req_per_s"] if best else None,
                                  "engine_p99_ms": best["p99_ms"] if best else None,
                                  "one_at_a_time_req_per_s": base_cap,
                                  "ratio": round(best["req_per_s"] / base_cap, 3) if best else None}
+    res["overheads"] = serve_overheads(serve, graphs, trees)
     return res
+
+
+def serve_overheads(serve, graphs, trees, lone=100, gap_s=0.004):
+    """What a step boundary costs, against the resident kernel's admission:
+    an engine step with nothing to admit or run (the replayed step graph, its
+    copies and the host's wait), and the latency of a lone small request (the
+    smallest tree's descendants; arrivals `gap_s` apart, so each runs alone)
+    under the stepped server and under the resident one."""
+    import torch
+
+    srv = serve.Server(graphs, trees, waves_per_step=32)
+    srv.h_count[0] = 0
+    for _ in range(10):
+        srv.step()
+    ts = []
+    for _ in range(200):
+        t = time.perf_counter()
+        srv.step()
+        ts.append(time.perf_counter() - t)
+    small = int(np.argmin([t.n for t in trees]))
+    reqs = [serve.Request(serve.dpc.JOB_TREE_DESCENDANTS, small, 0, k * gap_s) for k in range(lone)]
+    out = {"empty_step_us_median": round(float(np.median(ts)) * 1e6, 1),
+           "lone_request": f"descendants of a {trees[small].n}-node tree, {lone} requests {gap_s * 1e3:g} ms apart"}
+    srv.run(reqs[:8])
+    srv.reset()
+    r = srv.run(reqs)
+    out["stepped_p50_us"] = round(float(np.median(r.latencies(np.array([q.arrival for q in reqs])))) * 1e6, 1)
+    del srv
+    rsrv = serve.ResidentServer(graphs, trees)
+    rsrv.run(reqs[:8])
+    rsrv.reset()
+    r = rsrv.run(reqs)
+    out["resident_p50_us"] = round(float(np.median(r.latencies(np.array([q.arrival for q in reqs])))) * 1e6, 1)
+    out["resident_kernel_launches"] = r.steps
+    del rsrv
+    torch.cuda.empty_cache()
+    return out
 
 
 SERVE_P99_MS = 10.0  # tail latency at which the served stream's capacity is stated

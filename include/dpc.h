@@ -371,7 +371,8 @@ dpc_status dpc_engine_workspace_size(int32_t slots, int32_t max_n, int32_t max_m
                                      size_t *bytes);
 
 /*
- * Reset an engine: every slot free. slot_state (device, `slots` int32) receives
+ * Reset an engine: every slot free. slot_state (`slots` int32, device memory or
+ * pinned host memory, which the engine uses through its device address) receives
  * 1 when a problem is admitted into a slot and 2 when its results are complete;
  * the engine never writes 0 after the reset, so the caller keeps the slot
  * bookkeeping (a slot whose state is 2 may be reused).
@@ -401,6 +402,67 @@ dpc_status dpc_engine_step(void *workspace, size_t workspace_bytes, int32_t slot
                            const dpc_tuning *tuning, const dpc_job *new_jobs, const int32_t *new_slots,
                            const int32_t *new_count, int32_t max_waves, int32_t *slot_state, dpc_stats *stats,
                            dpc_stream_t stream);
+
+/*
+ * Resident form of the engine: the kernel stays on the GPU and admits new
+ * problems while it runs, from a mailbox in the caller's pinned host memory,
+ * so an arrival joins the running waves with no kernel boundary in between
+ * (serving with continuous batching, arrivals folded into the running
+ * kernel). Like the engine itself, this has no counterpart in the paper.
+ *
+ * The mailbox is a ring of DPC_MAILBOX_CAP job descriptors with their slots.
+ * One host thread posts jobs (dpc_mailbox_post: the descriptor, then a
+ * release store of the posted count); the kernel reads the count at each
+ * wave barrier and admits the new jobs during the next wave (at most one per
+ * warp of its grid per wave), advancing `taken`; the mailbox holds both
+ * counts, so a kernel continues from whatever its mailbox says was taken. A
+ * slot may be posted to only while it is free: never used since
+ * dpc_engine_init, or reported 2 and set back to 0 by the host before the post.
+ */
+#define DPC_MAILBOX_CAP 1024
+
+typedef struct dpc_mailbox {
+  uint64_t posted;                  /* host: jobs posted so far */
+  uint32_t stop;                    /* host: 1 = return once idle */
+  uint32_t reserved0;
+  uint64_t taken;                   /* kernel: jobs admitted so far */
+  uint64_t reserved1[5];
+  dpc_job jobs[DPC_MAILBOX_CAP];    /* job i in jobs[i % DPC_MAILBOX_CAP] */
+  int32_t slots[DPC_MAILBOX_CAP];   /* and its slot */
+} dpc_mailbox;
+
+/* Empty mailbox (host memory; no GPU work). */
+dpc_status dpc_mailbox_init(dpc_mailbox *mailbox);
+
+/* Post one job into `slot` (host): DPC_ERR_OVERFLOW when DPC_MAILBOX_CAP jobs
+ * are posted and not yet taken. Single producer: one host thread posts. */
+dpc_status dpc_mailbox_post(dpc_mailbox *mailbox, const dpc_job *job, int32_t slot);
+
+/* Ask a resident kernel to return once it is idle (host). */
+dpc_status dpc_mailbox_stop(dpc_mailbox *mailbox);
+
+/* Jobs the kernel has admitted so far (host, acquire load). */
+dpc_status dpc_mailbox_taken(const dpc_mailbox *mailbox, uint64_t *taken);
+
+/*
+ * Launch the engine in resident form on `stream` (returns at once). mailbox
+ * and slot_state (`slots` int32) must be pinned host memory that the device
+ * can address (cudaHostAlloc, or pinned memory under unified addressing;
+ * anything else is DPC_ERR_INVALID_ARG); slot_state receives 1 when a posted
+ * job is admitted and 2, after a system-scope fence, when its results are
+ * complete, so the host can poll it while the kernel runs. Results are in
+ * device memory: read them on another stream (the kernel's stream is busy
+ * until it returns). The kernel returns when it is idle (nothing queued,
+ * active or posted) and either the mailbox's stop flag is set or `limit_us`
+ * have passed since its start; or after 4 x limit_us even when busy; or on a
+ * device error (stats->status). It returns with its queue intact:
+ * dpc_engine_serve (or dpc_engine_step) continues the work. limit_us in
+ * [1, 10,000,000]. Workspace, slots, sizes and tuning as for dpc_engine_step,
+ * after dpc_engine_init with the same slot_state array.
+ */
+dpc_status dpc_engine_serve(void *workspace, size_t workspace_bytes, int32_t slots, int32_t max_n, int32_t max_m,
+                            const dpc_tuning *tuning, dpc_mailbox *mailbox, uint32_t limit_us, int32_t *slot_state,
+                            dpc_stats *stats, dpc_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,18 @@
 // can fold arrivals into the running work between steps (continuous batching).
 // All per-step arguments live in device memory, so a step can be captured in
 // a CUDA graph and replayed.
+//
+// Resident form (dpc_engine_serve): the kernel stays on the GPU and takes new
+// problems from a mailbox in host memory while it runs. The host posts a job
+// (descriptor and slot) and publishes it by a release store of the posted
+// count; at every wave barrier the last arriving block reads that count, and
+// during the next wave one warp per new job admits it into the list of the
+// wave after. Finished slots are reported in host memory, so the host sees
+// each result the moment it is complete, with no kernel boundary between an
+// arrival and its first wave. Every wait is bounded: an idle engine polls the
+// mailbox for at most kIdlePollNs per barrier, and the kernel returns once
+// it has been idle past its lifetime (or, busy or not, past four lifetimes),
+// with its queue intact.
 #include <climits>
 #include <cstring>
 #include <mutex>
@@ -65,6 +77,11 @@ struct EngineHeader {
   unsigned snap_status;          // and the status, so every block takes the same decision
   long long wave;                // waves run since init
   int slots, max_n, max_m, threshold, chunk, tree_chunk;
+  // resident form: the range [snap_lo, snap_hi) of mailbox jobs admitted
+  // during the coming wave, the exit decision and the start time
+  unsigned long long snap_lo, snap_hi;
+  int snap_exit;
+  unsigned long long t_start;
   unsigned long long task_cap;   // capacity of one task list
   unsigned long long slot_bytes; // scratch bytes per slot
 };
@@ -88,7 +105,20 @@ struct Engine {
   unsigned char *scratch;
   int *slot_state;   // caller's array: 1 running, 2 finished
   dpc_stats *stats;
+  dpc_mailbox *mb;   // resident form: the host's mailbox (else null)
+  unsigned long long limit_ns;  // resident form: the kernel's lifetime when idle
 };
+
+// Resident form: the longest an idle engine polls the mailbox at one barrier
+// (the other blocks wait at that barrier meanwhile, far below its own limit).
+constexpr unsigned long long kIdlePollNs = 20000;
+
+// Finished: results complete, then the state the caller polls. The state may
+// live in host memory (resident form), hence the system-scope fence.
+__device__ __forceinline__ void report_done(const Engine &e, int s) {
+  __threadfence_system();
+  *reinterpret_cast<volatile int *>(e.slot_state + s) = 2;
+}
 
 __device__ __forceinline__ void eng_fail(const Engine &e, unsigned code) {
   atomicCAS(&e.hdr->status, 0u, code);
@@ -412,8 +442,7 @@ __device__ void transition(const Engine &e, int s, int nl) {
   }
   if (done && lane == 0) {
     sl.phase = P_DONE;
-    __threadfence();
-    e.slot_state[s] = 2;
+    report_done(e, s);
     atomicSub(&e.hdr->active, 1);
   }
   __syncwarp();
@@ -621,7 +650,7 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
     if (lane == 0) {
       eng_fail(e, DPC_ERR_INVALID_ARG);
       e.slots[s].phase = P_DONE;
-      e.slot_state[s] = 2;
+      report_done(e, s);
     }
     __syncwarp();
     return;
@@ -634,7 +663,7 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
     sl.nf = 0;
     sl.next_count = 0;
     sl.post_level = 0;
-    e.slot_state[s] = 1;
+    *reinterpret_cast<volatile int *>(e.slot_state + s) = 1;
     atomicAdd(&e.hdr->active, 1);
   }
   __syncwarp();
@@ -663,8 +692,7 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
     if (nu == 0) {
       if (lane == 0) {
         sl.phase = P_DONE;
-        __threadfence();
-        e.slot_state[s] = 2;
+        report_done(e, s);
         atomicSub(&e.hdr->active, 1);
       }
       __syncwarp();
@@ -679,6 +707,54 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
 // block to arrive snapshots the next wave's task count, the active count and
 // the status before it releases the others: they cannot change until every
 // block has read them (no block can reach the next release before all arrive).
+// The mailbox's posted count, read with acquire semantics at system scope (the
+// host's release store of the count orders its job descriptors before it).
+__device__ __forceinline__ unsigned long long mailbox_posted(const dpc_mailbox *mb) {
+  const unsigned long long v = *reinterpret_cast<const volatile unsigned long long *>(&mb->posted);
+  __threadfence_system();
+  return v;
+}
+
+// Resident form, by the barrier's last arriver: which mailbox jobs the coming
+// wave admits (at most one per warp of the grid) and whether the kernel ends.
+// An engine with nothing queued, active or posted polls the mailbox for up to
+// kIdlePollNs; it ends on the host's stop request, or once its lifetime has
+// passed. A busy engine ends after four lifetimes (its queue stays intact).
+__device__ void serve_decision(const Engine &e, unsigned long long next_tasks, int active, unsigned status) {
+  EngineHeader &h = *e.hdr;
+  const unsigned long long now = global_ns();
+  if (h.t_start == 0) h.t_start = now;
+  const unsigned long long age = now - h.t_start;
+  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / kWarp);
+  const unsigned long long cap = DPC_MAILBOX_CAP < warps ? DPC_MAILBOX_CAP : warps;
+  // the mailbox keeps its own count of admitted jobs (only this kernel writes it)
+  unsigned long long lo = *reinterpret_cast<const volatile unsigned long long *>(&e.mb->taken);
+  unsigned long long posted = mailbox_posted(e.mb);
+  int exit_now = status != 0u || age > 4 * e.limit_ns;
+  if (!exit_now && next_tasks == 0 && active != 0) {
+    // an admitted problem with no task queued can never finish (a bug or malformed input)
+    eng_fail(e, DPC_ERR_DEVICE);
+    exit_now = 1;
+  }
+  if (!exit_now && next_tasks == 0 && active == 0 && posted == lo) {  // idle
+    const unsigned stop = *reinterpret_cast<const volatile unsigned *>(&e.mb->stop);
+    if (stop || age > e.limit_ns) {
+      exit_now = 1;
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (posted == lo && global_ns() - t0 < kIdlePollNs) {
+        __nanosleep(256);
+        posted = mailbox_posted(e.mb);
+      }
+    }
+  }
+  const unsigned long long hi = exit_now ? lo : (posted - lo > cap ? lo + cap : posted);
+  h.snap_lo = lo;
+  h.snap_hi = hi;
+  *reinterpret_cast<volatile unsigned long long *>(&e.mb->taken) = hi;
+  h.snap_exit = exit_now;
+}
+
 __device__ bool grid_barrier(const Engine &e, int next_list) {
   __shared__ int s_ok;
   __syncthreads();
@@ -692,6 +768,7 @@ __device__ bool grid_barrier(const Engine &e, int next_list) {
       e.hdr->snap_count = next_list >= 0 ? *reinterpret_cast<volatile unsigned long long *>(&e.hdr->count[next_list]) : 0;
       e.hdr->snap_active = *reinterpret_cast<volatile int *>(&e.hdr->active);
       e.hdr->snap_status = *reinterpret_cast<volatile unsigned *>(&e.hdr->status);
+      if (e.mb) serve_decision(e, e.hdr->snap_count, e.hdr->snap_active, e.hdr->snap_status);
       e.hdr->bar_count = 0;
       __threadfence();
       atomicAdd(&e.hdr->bar_gen, 1u);
@@ -720,6 +797,8 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
                                                      const int *__restrict__ new_count, int max_waves) {
   __shared__ int s_stage[256 / kWarp][kEngStage + 1];
   const int lane = lane_id();
+  // resident form: this launch's lifetime starts at its first barrier
+  if (e.mb && blockIdx.x == 0 && threadIdx.x == 0) e.hdr->t_start = 0;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const EngStage st{s_stage[threadIdx.x >> 5], &s_stage[threadIdx.x >> 5][kEngStage]};
@@ -732,7 +811,8 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
     const int na = new_count ? *new_count : 0;
     for (int i = gw; i < na; i += nw) admit(e, new_jobs[i], new_slots[i], l);
   }
-  if (!grid_barrier(e, -1)) return;
+  // (resident form: the barrier's last arriver also takes the first mailbox posts)
+  if (!grid_barrier(e, e.mb ? (int)(wave % 3) : -1)) return;
   unsigned long long relaxed = 0;
   for (int w = 0; w < max_waves; ++w, ++wave) {
     const int l = (int)(wave % 3), nl = (int)((wave + 1) % 3), ol = (int)((wave + 2) % 3);
@@ -740,6 +820,20 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       e.hdr->count[ol] = 0;
       e.hdr->cursor[ol] = 0;
+    }
+    if (e.mb) {
+      // resident form: the jobs posted before the barrier, one warp each, into the next wave's list
+      const unsigned long long lo = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->snap_lo);
+      const unsigned long long hi = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->snap_hi);
+      if ((unsigned long long)gw < hi - lo) {
+        const unsigned long long q = (lo + (unsigned long long)gw) % DPC_MAILBOX_CAP;
+        dpc_job job;
+        const int4 *src = reinterpret_cast<const int4 *>(&e.mb->jobs[q]);
+        int4 *dst = reinterpret_cast<int4 *>(&job);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(dpc_job) / sizeof(int4)); ++k) dst[k] = __ldcv(src + k);
+        admit(e, job, __ldcv(&e.mb->slots[q]), nl);
+      }
     }
     const unsigned long long n = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->count[l]);
     // tasks are handed out kGrab at a time while many remain, one at a time near
@@ -779,6 +873,14 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
     const unsigned long long nn = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->snap_count);
     const int active = *reinterpret_cast<volatile int *>(&e.hdr->snap_active);
     const unsigned status = *reinterpret_cast<volatile unsigned *>(&e.hdr->snap_status);
+    if (e.mb) {
+      // resident form: idle waves go on (the barrier polled the mailbox) until the exit decision
+      if (*reinterpret_cast<volatile int *>(&e.hdr->snap_exit)) {
+        ++wave;
+        break;
+      }
+      continue;
+    }
     if (nn == 0 || status != 0u) {
       // no task for the next wave: either every problem is finished, or one can
       // never finish (a bug or malformed input) - stop rather than spin on empty waves
@@ -813,6 +915,9 @@ __global__ void engine_reset(EngineHeader *h, Slot *slots, int nslots, int *slot
     h->status = 0;
     h->active = 0;
     h->wave = 0;
+    h->snap_lo = h->snap_hi = 0;
+    h->snap_exit = 0;
+    h->t_start = 0;
     h->slots = nslots;
     h->max_n = max_n;
     h->max_m = max_m;
@@ -900,6 +1005,18 @@ int engine_grid(int dev) {
   return g_eng_blocks[dev];
 }
 
+// slot_state may be device memory or pinned host memory (the resident form's
+// host polls it); a pinned host array is used through its device address.
+int32_t *state_for_device(int32_t *slot_state) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, slot_state) != cudaSuccess) {
+    cudaGetLastError();
+    return slot_state;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<int32_t *>(a.devicePointer);
+  return slot_state;
+}
+
 Engine engine_view(void *ws, int slots, const Layout &L, int *slot_state, dpc_stats *stats) {
   Engine e;
   char *b = static_cast<char *>(ws);
@@ -910,6 +1027,8 @@ Engine engine_view(void *ws, int slots, const Layout &L, int *slot_state, dpc_st
   e.scratch = reinterpret_cast<unsigned char *>(b + L.scratch);
   e.slot_state = slot_state;
   e.stats = stats;
+  e.mb = nullptr;
+  e.limit_ns = 0;
   (void)slots;
   return e;
 }
@@ -940,6 +1059,7 @@ dpc_status dpc_engine_init(void *workspace, size_t workspace_bytes, int32_t slot
   const Layout L = layout_for(slots, max_n, max_m, c.threshold, c.chunk, c.tree_chunk);
   if (!workspace || workspace_bytes < L.total) return DPC_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  slot_state = state_for_device(slot_state);
   Engine e = engine_view(workspace, slots, L, slot_state, nullptr);
   engine_reset<<<ceil_div(slots, 256), 256, 0, s>>>(e.hdr, e.slots, slots, slot_state, c.threshold, c.chunk,
                                                   c.tree_chunk, max_n, max_m, L.task_cap, L.slot_bytes);
@@ -966,8 +1086,79 @@ dpc_status dpc_engine_step(void *workspace, size_t workspace_bytes, int32_t slot
                                                                                           : full;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (stats && cudaMemsetAsync(stats, 0, sizeof(dpc_stats), s) != cudaSuccess) return DPC_ERR_CUDA;
-  Engine e = engine_view(workspace, slots, L, slot_state, stats);
+  Engine e = engine_view(workspace, slots, L, state_for_device(slot_state), stats);
   void *args[] = {&e, (void *)&new_jobs, (void *)&new_slots, (void *)&new_count, &max_waves};
+  // cooperative launch: every block is resident, so the grid barrier cannot deadlock
+  if (cudaLaunchCooperativeKernel((const void *)engine_kernel, dim3(blocks), dim3(256), args, 0, s) != cudaSuccess) {
+    cudaGetLastError();
+    return DPC_ERR_CUDA;
+  }
+  return DPC_OK;
+}
+
+dpc_status dpc_mailbox_init(dpc_mailbox *mailbox) {
+  if (!mailbox) return DPC_ERR_INVALID_ARG;
+  std::memset(static_cast<void *>(mailbox), 0, sizeof(dpc_mailbox));
+  return DPC_OK;
+}
+
+dpc_status dpc_mailbox_post(dpc_mailbox *mailbox, const dpc_job *job, int32_t slot) {
+  if (!mailbox || !job || slot < 0) return DPC_ERR_INVALID_ARG;
+  const uint64_t p = __atomic_load_n(&mailbox->posted, __ATOMIC_RELAXED);  // the only writer
+  const uint64_t t = __atomic_load_n(&mailbox->taken, __ATOMIC_ACQUIRE);
+  if (p - t >= (uint64_t)DPC_MAILBOX_CAP) return DPC_ERR_OVERFLOW;
+  mailbox->jobs[p % DPC_MAILBOX_CAP] = *job;
+  mailbox->slots[p % DPC_MAILBOX_CAP] = slot;
+  // the descriptor (and every earlier store of this thread, such as the
+  // slot's state set back to 0) before the count that publishes it
+  __atomic_store_n(&mailbox->posted, p + 1, __ATOMIC_RELEASE);
+  return DPC_OK;
+}
+
+dpc_status dpc_mailbox_stop(dpc_mailbox *mailbox) {
+  if (!mailbox) return DPC_ERR_INVALID_ARG;
+  __atomic_store_n(&mailbox->stop, 1u, __ATOMIC_RELEASE);
+  return DPC_OK;
+}
+
+dpc_status dpc_mailbox_taken(const dpc_mailbox *mailbox, uint64_t *taken) {
+  if (!mailbox || !taken) return DPC_ERR_INVALID_ARG;
+  *taken = __atomic_load_n(&mailbox->taken, __ATOMIC_ACQUIRE);
+  return DPC_OK;
+}
+
+dpc_status dpc_engine_serve(void *workspace, size_t workspace_bytes, int32_t slots, int32_t max_n, int32_t max_m,
+                            const dpc_tuning *tuning, dpc_mailbox *mailbox, uint32_t limit_us, int32_t *slot_state,
+                            dpc_stats *stats, dpc_stream_t stream) {
+  if (slots < 1 || max_n < 1 || max_m < 0 || !mailbox || !slot_state || limit_us < 1 || limit_us > 10000000u)
+    return DPC_ERR_INVALID_ARG;
+  EngineCfg c;
+  dpc_status st = engine_cfg(tuning, &c);
+  if (st != DPC_OK) return st;
+  const Layout L = layout_for(slots, max_n, max_m, c.threshold, c.chunk, c.tree_chunk);
+  if (!workspace || workspace_bytes < L.total) return DPC_ERR_WORKSPACE;
+  // the mailbox and the slot states must be pinned host memory the device can address
+  void *d_mb = nullptr, *d_state = nullptr;
+  if (cudaHostGetDevicePointer(&d_mb, mailbox, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&d_state, slot_state, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return DPC_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DPC_ERR_CUDA;
+  const int full = engine_grid(dev);
+  if (full <= 0) return DPC_ERR_CUDA;
+  const int blocks = (tuning && tuning->parent_blocks > 0 && tuning->parent_blocks < full) ? tuning->parent_blocks
+                                                                                          : full;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (stats && cudaMemsetAsync(stats, 0, sizeof(dpc_stats), s) != cudaSuccess) return DPC_ERR_CUDA;
+  Engine e = engine_view(workspace, slots, L, static_cast<int *>(d_state), stats);
+  e.mb = static_cast<dpc_mailbox *>(d_mb);
+  e.limit_ns = (unsigned long long)limit_us * 1000ull;
+  const dpc_job *no_jobs = nullptr;
+  const int32_t *no_slots = nullptr, *no_count = nullptr;
+  int max_waves = INT_MAX;
+  void *args[] = {&e, (void *)&no_jobs, (void *)&no_slots, (void *)&no_count, &max_waves};
   // cooperative launch: every block is resident, so the grid barrier cannot deadlock
   if (cudaLaunchCooperativeKernel((const void *)engine_kernel, dim3(blocks), dim3(256), args, 0, s) != cudaSuccess) {
     cudaGetLastError();

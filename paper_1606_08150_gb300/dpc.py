@@ -34,7 +34,8 @@ EXPORTS = (
     "dpc_pagerank_workspace_size", "dpc_pagerank",
     "dpc_bfs_rec_workspace_size", "dpc_bfs_rec",
     "dpc_graph_coloring_workspace_size", "dpc_graph_coloring",
-    "dpc_engine_workspace_size", "dpc_engine_init", "dpc_engine_step",
+    "dpc_engine_workspace_size", "dpc_engine_init", "dpc_engine_step", "dpc_engine_serve",
+    "dpc_mailbox_init", "dpc_mailbox_post", "dpc_mailbox_stop", "dpc_mailbox_taken",
     "dpc_wait_selftest", "dpc_gather_rate",
 )
 
@@ -55,6 +56,17 @@ class Job(ctypes.Structure):
 
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("source", ctypes.c_int32),
                 ("off", ctypes.c_void_p), ("col", ctypes.c_void_p), ("w", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+MAILBOX_CAP = 1024  # DPC_MAILBOX_CAP
+
+
+class MailboxLayout(ctypes.Structure):
+    """dpc_mailbox: the resident engine's ring of posted jobs (host memory)."""
+
+    _fields_ = [("posted", ctypes.c_uint64), ("stop", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("taken", ctypes.c_uint64), ("reserved1", ctypes.c_uint64 * 5), ("jobs", Job * MAILBOX_CAP),
+                ("slots", ctypes.c_int32 * MAILBOX_CAP)]
 
 
 class Stats(ctypes.Structure):
@@ -122,6 +134,16 @@ def _load_library() -> ctypes.CDLL:
     lib.dpc_engine_init.restype = st
     lib.dpc_engine_step.argtypes = [P, sz, i32, i32, i32, P, P, P, P, i32, P, P, P]
     lib.dpc_engine_step.restype = st
+    lib.dpc_engine_serve.argtypes = [P, sz, i32, i32, i32, P, P, ctypes.c_uint32, P, P, P]
+    lib.dpc_engine_serve.restype = st
+    lib.dpc_mailbox_init.argtypes = [P]
+    lib.dpc_mailbox_init.restype = st
+    lib.dpc_mailbox_post.argtypes = [P, P, i32]
+    lib.dpc_mailbox_post.restype = st
+    lib.dpc_mailbox_stop.argtypes = [P]
+    lib.dpc_mailbox_stop.restype = st
+    lib.dpc_mailbox_taken.argtypes = [P, P]
+    lib.dpc_mailbox_taken.restype = st
     lib.dpc_gather_rate.argtypes = [P, i32, i32, P, P, P]
     lib.dpc_gather_rate.restype = st
     lib.dpc_wait_selftest.argtypes = [ctypes.c_uint32, P, P]
@@ -422,10 +444,19 @@ def engine_workspace_size(slots: int, max_n: int, max_m: int, tuning: Optional[T
     return int(out.value)
 
 
+def _state_ptr(t: torch.Tensor):
+    """slot_state: a CUDA tensor, or a pinned host tensor (the resident form's)."""
+    if t.is_cuda:
+        return _dptr(t, torch.int32, "slot_state")
+    if not t.is_pinned() or t.dtype != torch.int32 or not t.is_contiguous():
+        raise ValueError("slot_state must be a CUDA int32 tensor or a pinned, contiguous host int32 tensor")
+    return t.data_ptr()
+
+
 def engine_init(workspace: torch.Tensor, slots: int, max_n: int, max_m: int, slot_state: torch.Tensor,
                 tuning: Optional[Tuning] = None, stream: Optional[torch.cuda.Stream] = None) -> None:
     _check(_lib.dpc_engine_init(workspace.data_ptr(), workspace.numel(), slots, max_n, max_m, _tuning(tuning),
-                                _dptr(slot_state, torch.int32, "slot_state"), _stream(stream)), "dpc_engine_init")
+                                _state_ptr(slot_state), _stream(stream)), "dpc_engine_init")
 
 
 def engine_step(workspace: torch.Tensor, slots: int, max_n: int, max_m: int, new_jobs: Optional[torch.Tensor],
@@ -437,8 +468,45 @@ def engine_step(workspace: torch.Tensor, slots: int, max_n: int, max_m: int, new
     _check(_lib.dpc_engine_step(workspace.data_ptr(), workspace.numel(), slots, max_n, max_m, _tuning(tuning),
                                 new_jobs.data_ptr() if new_jobs is not None else None,
                                 _dptr(new_slots, torch.int32, "new_slots"), _dptr(new_count, torch.int32, "new_count"),
-                                max_waves, _dptr(slot_state, torch.int32, "slot_state"),
+                                max_waves, _state_ptr(slot_state),
                                 _dptr(stats, torch.uint8, "stats"), _stream(stream)), "dpc_engine_step")
+
+
+class Mailbox:
+    """The resident engine's mailbox (dpc_mailbox) in pinned host memory. One
+    host thread posts; the running kernel admits what was posted at its next
+    wave barrier."""
+
+    def __init__(self):
+        self.buf = torch.zeros(ctypes.sizeof(MailboxLayout), dtype=torch.uint8).pin_memory()
+        self.ptr = self.buf.data_ptr()
+        _check(_lib.dpc_mailbox_init(self.ptr), "dpc_mailbox_init")
+
+    def post(self, job: Job, slot: int) -> None:
+        _check(_lib.dpc_mailbox_post(self.ptr, ctypes.byref(job), int(slot)), "dpc_mailbox_post")
+
+    def stop(self) -> None:
+        _check(_lib.dpc_mailbox_stop(self.ptr), "dpc_mailbox_stop")
+
+    def clear_stop(self) -> None:
+        """Undo stop(); only while no resident kernel runs on this mailbox."""
+        MailboxLayout.from_address(self.ptr).stop = 0
+
+    def taken(self) -> int:
+        out = ctypes.c_uint64(0)
+        _check(_lib.dpc_mailbox_taken(self.ptr, ctypes.byref(out)), "dpc_mailbox_taken")
+        return int(out.value)
+
+
+def engine_serve(workspace: torch.Tensor, slots: int, max_n: int, max_m: int, mailbox: Mailbox, limit_us: int,
+                 slot_state: torch.Tensor, tuning: Optional[Tuning] = None, stats: Optional[torch.Tensor] = None,
+                 stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Launch the resident engine (returns at once); slot_state: pinned host int32."""
+    if slot_state.is_cuda:
+        raise ValueError("the resident engine reports in pinned host memory: slot_state must be a pinned host tensor")
+    _check(_lib.dpc_engine_serve(workspace.data_ptr(), workspace.numel(), slots, max_n, max_m, _tuning(tuning),
+                                 mailbox.ptr, int(limit_us), _state_ptr(slot_state), _dptr(stats, torch.uint8, "stats"),
+                                 _stream(stream)), "dpc_engine_serve")
 
 
 def pack_jobs(jobs) -> bytes:

@@ -9,6 +9,12 @@ work already on the GPU at the next step: their tasks share the waves of the
 running ones. The engine step is a CUDA graph replayed every step, between an
 asynchronous copy of the admissions in and of the slot states out.
 
+ResidentServer keeps the engine on the GPU instead (dpc_engine_serve): an
+arrival is posted to the running kernel's mailbox in pinned host memory and
+joins the waves at the kernel's next wave barrier, with no step boundary and
+no launch in between; completions are read from pinned host memory while the
+kernel runs.
+
 The one-at-a-time baseline serves the same stream with one library call per
 request (grid-level consolidation), each waited for before the next.
 
@@ -210,6 +216,101 @@ class Server:
                 free.append(s)
         makespan = time.perf_counter() - t0
         return ServeResult(admitted, finished, steps, self.slots, makespan, dpc.read_stats(self.stats).status, slot_of)
+
+
+class ResidentServer(Server):
+    """Server whose engine stays resident: arrivals are folded into the running
+    kernel through its mailbox (dpc_engine_serve). The kernel returns when it
+    has been idle for `limit_us` (or is asked to stop at the end of a stream);
+    the loop launches it again when work arrives after that."""
+
+    def __init__(self, graphs: Sequence[Resident], trees: Sequence[Resident], slots: Optional[int] = None,
+                 tuning: Optional[dpc.Tuning] = None, memory_fraction: float = 0.5, max_slots: int = 128,
+                 limit_us: int = 100_000):
+        self.limit_us = int(limit_us)
+        super().__init__(graphs, trees, slots=slots, waves_per_step=1, tuning=tuning,
+                         memory_fraction=memory_fraction, max_slots=max_slots, use_graph=False)
+        self.launches = 0
+
+    def reset(self) -> None:
+        # the kernel reports admissions and completions here, in pinned host memory
+        self.state_host = torch.zeros(self.slots, dtype=torch.int32).pin_memory()
+        self.mailbox = dpc.Mailbox()
+        # result reads while the kernel runs: a side stream and a pinned buffer, made
+        # here because allocating page-locked memory can serialise streams
+        self.side = torch.cuda.Stream()
+        self.read_buf = torch.empty(self.max_n, dtype=torch.int32).pin_memory()
+        with torch.cuda.stream(self.stream):
+            dpc.engine_init(self.ws, self.slots, self.max_n, self.max_m, self.state_host, self.tuning)
+        self.stream.synchronize()
+
+    def _launch(self) -> None:
+        dpc.engine_serve(self.ws, self.slots, self.max_n, self.max_m, self.mailbox, self.limit_us, self.state_host,
+                         self.tuning, self.stats, self.stream)
+        self.launches += 1
+
+    def read_out(self, slot: int, n: int) -> np.ndarray:
+        """A copy of slot `slot`'s first n results (int32), read on the side
+        stream (the kernel's stream is busy while it runs)."""
+        with torch.cuda.stream(self.side):
+            self.read_buf[:n].copy_(self.out[slot, :n], non_blocking=True)
+        self.side.synchronize()
+        return self.read_buf[:n].numpy().copy()
+
+    def run(self, requests: Sequence[Request], on_done=None) -> ServeResult:
+        """Serve a request stream in arrival order; `on_done(i, slot)` is called
+        when request i's results sit in self.out[slot] (read them with
+        read_out: the kernel may still be running)."""
+        order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+        n = len(requests)
+        admitted = np.zeros(n)
+        finished = np.zeros(n)
+        slot_of = np.full(n, -1, np.int64)
+        free = list(range(self.slots))
+        running = {}
+        state = self.state_host.numpy()
+        nxt = 0
+        polls = 0
+        self.stream.synchronize()  # no kernel of an earlier run is still on the mailbox
+        self.mailbox.clear_stop()
+        t0 = time.perf_counter()
+        self._launch()
+        while nxt < n or running:
+            now = time.perf_counter() - t0
+            posted = False
+            while nxt < n and free and requests[order[nxt]].arrival <= now:
+                i = order[nxt]
+                s = free.pop()
+                state[s] = 0  # before the post, whose release store orders it
+                self.mailbox.post(self.job_for(requests[i], s), s)
+                running[s] = i
+                admitted[i] = now
+                slot_of[i] = s
+                nxt += 1
+                posted = True
+            if running:
+                done = [s for s in np.nonzero(state == 2)[0].tolist() if s in running]
+                if done:
+                    t_done = time.perf_counter() - t0
+                    for s in done:
+                        i = running.pop(s)
+                        finished[i] = t_done
+                        if on_done is not None:
+                            on_done(i, s)
+                        free.append(s)
+            polls += 1
+            if (posted or (running and polls % 64 == 0)) and self.stream.query():
+                # the kernel returned (its lifetime passed, or a device error): check, then relaunch
+                st = dpc.read_stats(self.stats).status
+                if st != dpc.OK:
+                    raise dpc.DpcError(st, "resident engine")
+                if any(state[s] != 2 for s in running) or nxt < n:
+                    self._launch()
+        self.mailbox.stop()
+        self.stream.synchronize()
+        makespan = time.perf_counter() - t0
+        return ServeResult(admitted, finished, self.launches, self.slots, makespan,
+                           dpc.read_stats(self.stats).status, slot_of)
 
 
 def server_from_cache(cache, graphs: Sequence[Resident], trees: Sequence[Resident], sssp_fraction: float = 0.6,

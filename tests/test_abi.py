@@ -65,6 +65,7 @@ def test_binding_constants_match_the_header():
     # the size of the allocation-free entry point's array, (size_t)A << B in the header
     a, b = re.search(r"#define DPC_NOALLOC_SCRATCH_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)", text).groups()
     assert dpc.NOALLOC_SCRATCH_BYTES == int(a) << int(b)
+    assert dpc.MAILBOX_CAP == int(re.search(r"#define DPC_MAILBOX_CAP\s+(\d+)", text).group(1))
     # struct layouts: the C compiler's sizes and offsets against the ctypes mirrors
     import shutil
     import subprocess
@@ -72,7 +73,8 @@ def test_binding_constants_match_the_header():
 
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
-    fields = [("dpc_tuning", dpc.Tuning), ("dpc_stats", dpc.Stats)]
+    fields = [("dpc_tuning", dpc.Tuning), ("dpc_stats", dpc.Stats), ("dpc_job", dpc.Job),
+              ("dpc_mailbox", dpc.MailboxLayout)]
     lines = ['#include "dpc.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
     for cname, cls in fields:
         lines.append(f'  printf("%zu\\n", sizeof({cname}));')
@@ -160,3 +162,37 @@ def test_bad_tuning_rejected(lib):
     assert lib.dpc_spmv_csr_workspace_size(100, 100, 4, ctypes.byref(t), ctypes.byref(out)) == 1
     t = dpc.Tuning(chunk=-5)
     assert lib.dpc_spmv_csr_workspace_size(100, 100, 4, ctypes.byref(t), ctypes.byref(out)) == 1
+
+
+def test_mailbox_host_side(lib):
+    """The mailbox calls are host code: posting fills the ring in order and
+    publishes the count, a full ring (DPC_MAILBOX_CAP posted, none taken) is
+    refused, stop sets the flag; bad arguments are rejected."""
+    from paper_1606_08150_gb300 import dpc
+
+    mb = dpc.MailboxLayout()
+    P = ctypes.c_void_p
+    lib.dpc_mailbox_init.argtypes = [P]
+    lib.dpc_mailbox_post.argtypes = [P, P, ctypes.c_int32]
+    lib.dpc_mailbox_stop.argtypes = [P]
+    lib.dpc_mailbox_taken.argtypes = [P, P]
+    addr = ctypes.addressof(mb)
+    mb.posted = 99
+    assert lib.dpc_mailbox_init(addr) == 0 and mb.posted == 0 and mb.taken == 0 and mb.stop == 0
+    for i in range(dpc.MAILBOX_CAP):
+        job = dpc.Job(dpc.JOB_SSSP, 10 + i, 20, i % 7, 0x1000, 0x2000, 0x3000, 0x4000)
+        assert lib.dpc_mailbox_post(addr, ctypes.byref(job), i % 5) == 0
+    assert mb.posted == dpc.MAILBOX_CAP
+    assert [mb.jobs[i].n for i in (0, 1, dpc.MAILBOX_CAP - 1)] == [10, 11, 10 + dpc.MAILBOX_CAP - 1]
+    assert mb.slots[7] == 2 and mb.jobs[7].source == 0
+    job = dpc.Job(dpc.JOB_SSSP, 1, 0, 0, 0x1000, 0, 0, 0x4000)
+    assert lib.dpc_mailbox_post(addr, ctypes.byref(job), 0) == dpc.ERR_OVERFLOW  # ring full
+    mb.taken = 3  # the kernel admitted three: room for three more, in the ring's first entries
+    assert lib.dpc_mailbox_post(addr, ctypes.byref(job), 4) == 0
+    assert mb.posted == dpc.MAILBOX_CAP + 1 and mb.jobs[0].n == 1 and mb.slots[0] == 4
+    got = ctypes.c_uint64(0)
+    assert lib.dpc_mailbox_taken(addr, ctypes.byref(got)) == 0 and got.value == 3
+    assert lib.dpc_mailbox_stop(addr) == 0 and mb.stop == 1
+    assert lib.dpc_mailbox_post(addr, None, 0) == dpc.ERR_INVALID_ARG
+    assert lib.dpc_mailbox_post(addr, ctypes.byref(job), -1) == dpc.ERR_INVALID_ARG
+    assert lib.dpc_mailbox_init(None) == dpc.ERR_INVALID_ARG

@@ -122,3 +122,65 @@ def test_slots_follow_free_memory(dpc):
     big = serve.slots_for_memory(1000, 16000, 512 << 20)
     assert 1 <= small <= big
     assert serve.slots_for_memory(1 << 22, 1 << 26, 1 << 20) == 0
+
+
+@pytest.mark.parametrize("rate,slots", [(20000.0, 6), (0.0, 16)])
+def test_resident_engine_folds_arrivals_into_the_running_kernel(dpc, pool, rate, slots):
+    """ResidentServer: one kernel launch serves the whole stream (arrivals are
+    admitted from the mailbox while it runs), and every result equals the
+    oracle's and the one served alone."""
+    graphs, graphs_h, sources, trees, trees_h = pool
+    rng = np.random.default_rng(9)
+    reqs = serve.poisson_stream(rng, 120, rate, len(graphs), len(trees), sources)
+    srv = serve.ResidentServer(graphs, trees, slots=slots, limit_us=2_000_000)
+    got = {}
+
+    def keep(i, s):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        got[i] = srv.read_out(s, n)
+
+    res = srv.run(reqs, on_done=keep)
+    assert res.status == 0
+    assert res.steps == 1  # kernel launches: the stream never waited for a new one
+    assert len(got) == len(reqs) and np.all(res.finished >= res.admitted)
+    assert srv.mailbox.taken() == len(reqs)
+    alone = {}
+
+    def keep_alone(i, out):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        alone[i] = out[:n].cpu().numpy().copy()
+
+    serve.one_at_a_time(graphs, trees, [serve.Request(r.kind, r.problem, r.source, 0.0) for r in reqs],
+                        on_done=keep_alone)
+    for i, r in enumerate(reqs):
+        want = expected(r, graphs_h, trees_h)
+        assert np.array_equal(got[i], want), i
+        assert np.array_equal(alone[i], got[i]), i
+
+
+def test_resident_engine_returns_when_idle_and_resumes(dpc, pool):
+    """With a short lifetime and arrivals far apart the resident kernel returns
+    while idle; the loop launches it again for the next arrival, and the
+    engine's state carries over: results stay exact."""
+    graphs, graphs_h, sources, trees, trees_h = pool
+    reqs = [serve.Request(dpc.JOB_TREE_HEIGHT, 1, 0, 0.0), serve.Request(dpc.JOB_SSSP, 2, int(sources[2][3]), 0.03),
+            serve.Request(dpc.JOB_TREE_DESCENDANTS, 3, 0, 0.06), serve.Request(dpc.JOB_SSSP, 4, int(sources[4][5]), 0.09)]
+    srv = serve.ResidentServer(graphs, trees, slots=4, limit_us=2000)
+    got = {}
+
+    def keep(i, s):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        got[i] = srv.read_out(s, n)
+
+    res = srv.run(reqs, on_done=keep)
+    assert res.status == 0 and len(got) == len(reqs)
+    assert res.steps >= 2  # relaunched after idle returns
+    for i, r in enumerate(reqs):
+        assert np.array_equal(got[i], expected(r, graphs_h, trees_h)), i
+
+
+def test_resident_engine_rejects_device_memory_for_the_mailbox_side(dpc, pool):
+    graphs, _, _, trees, _ = pool
+    srv = serve.ResidentServer(graphs[:1], trees[:1], slots=2)
+    with pytest.raises(ValueError):
+        dpc.engine_serve(srv.ws, srv.slots, srv.max_n, srv.max_m, srv.mailbox, 1000, srv.state, stream=srv.stream)
