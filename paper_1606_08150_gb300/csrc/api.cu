@@ -613,6 +613,7 @@ dpc_status dpc_sssp(const int32_t *off, const int32_t *col, const uint32_t *w, i
   // Without a split the frontier of round n is empty (Bellman-Ford's bound);
   // with one, the cap only keeps the round stamps below their sentinel.
   p.max_rounds = (c.delta || c.sub_delta) ? 0xFFFFFFF0u : (unsigned)n + 1u;
+  p.prebuffer = level == DPC_QUEUE ? 1 : 0;
   p.launch_budget = launch_budget(dev);
   sssp_carve(p, workspace, n, m, level, c);
   p.stats = stats;

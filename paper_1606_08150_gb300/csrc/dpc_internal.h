@@ -55,6 +55,7 @@ struct WsHeader {
   unsigned nf_split_old;           // S before the split in progress
   unsigned nf_dmin;                // smallest distance at or above S (split in progress)
   unsigned nf_done;                // 1: a split found no vertex at or above S (the run is over)
+  unsigned nf_append;              // queue level: 1 when the coming round's parent phase may buffer units
   // lines 8-15: the unit cursors of a consolidated loop (SpMV), one partition each
   alignas(128) unsigned long long cursors[kUnitCursors * kCursorStride];
 };
@@ -240,6 +241,7 @@ struct SsspParams {
   unsigned delta;     // near-far split width (0: no split)
   unsigned sub_delta; // sub-split width for vertices above the threshold (0: none)
   unsigned max_rounds;
+  int prebuffer;      // queue level: the commit buffers the units of the next round's heavy vertices
   long long launch_budget;
   int4 *fcur;         // frontier of the current round: (vertex, distance when the round began,
                       // first edge, end edge)

@@ -81,6 +81,7 @@ struct Phase {
   unsigned s;                // sub-split: a heavy frontier vertex is relaxed below it
   unsigned S_old;            // (split in progress) the split before it
   unsigned done;             // a split found no vertex at or above S
+  unsigned append;           // queue level: the round's parent phase may buffer units
 };
 __shared__ Phase s_ph;
 
@@ -94,6 +95,7 @@ __device__ __forceinline__ void phase_load(const SsspParams &p) {
   s_ph.s = ld_volatile(&h->nf_sub);
   s_ph.S_old = ld_volatile(&h->nf_split_old);
   s_ph.done = ld_volatile(&h->nf_done);
+  s_ph.append = ld_volatile(&h->nf_append);
 }
 
 // Every thread of the block; at the start of a device-launched kernel.
@@ -382,7 +384,53 @@ __device__ __forceinline__ bool relaxed_now(const SsspParams &p, const int4 &f, 
 struct NearAcc {
   unsigned long long elig = 0;
   unsigned hmin = kInf;
+  unsigned long long pre_edges = 0, pre_items = 0;  // heavy entries buffered ahead (prebuffer)
 };
+
+// Queue level (p.prebuffer): a heavy entry that the next round relaxes for
+// sure (below the sub-split, which never moves down) goes straight into the
+// unit buffer as its units, instead of into the frontier for the next round's
+// parent phase to buffer. The next round then needs no grid barrier between
+// its parent phase and its consolidated loop, unless the sub-split has to
+// advance first (then heavy frontier entries become eligible only in that
+// round: nf_append). Returns the entries it could not buffer (only when the
+// buffer overflows, which valid input cannot make happen).
+template <int N>
+__device__ __forceinline__ unsigned buffer_ahead(const SsspParams &p, unsigned pre, const int (&v)[N],
+                                                 const unsigned (&dv)[N], const int (&a)[N], const int (&b)[N],
+                                                 NearAcc &acc) {
+  int nu[N], mine = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    nu[j] = pre >> j & 1u ? ceil_div(b[j] - a[j], p.chunk) : 0;
+    mine += nu[j];
+  }
+  const int inc = warp_inclusive_scan(mine);
+  const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
+  if (total == 0) return 0u;
+  unsigned long long base = 0;
+  if (lane_id() == kWarp - 1) base = atomicAdd(&p.hdr->cursor, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, kWarp - 1);
+  if (base + (unsigned long long)total > (unsigned long long)p.max_units) {
+    if (lane_id() == 0) sssp_fail(p, DPC_ERR_OVERFLOW);
+    return pre;
+  }
+  int pos = (int)base + inc - mine;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    for (int q = 0; q < nu[j]; ++q) {
+      const int ua = a[j] + q * p.chunk;
+      p.units[pos + q] = make_int4(ua, min(b[j], ua + p.chunk), (int)dv[j], v[j]);
+    }
+    pos += nu[j];
+    if (nu[j]) {
+      acc.elig++;
+      acc.pre_items++;
+      acc.pre_edges += (unsigned long long)(b[j] - a[j]);
+    }
+  }
+  return 0u;
+}
 
 // A full warp appends up to N entries per lane (entry j when bit j of `near`
 // is set) to the next frontier: (v, d, first edge, end edge) at consecutive
@@ -391,6 +439,13 @@ template <int N>
 __device__ __forceinline__ void append_near(const SsspParams &p, unsigned near, const int (&v)[N],
                                             const unsigned (&dv)[N], const int (&a)[N], const int (&b)[N], unsigned s,
                                             NearAcc &acc) {
+  if (p.prebuffer) {
+    unsigned pre = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if ((near >> j & 1u) && b[j] - a[j] > p.threshold && dv[j] < s) pre |= 1u << j;
+    if (__any_sync(0xffffffffu, pre != 0)) near = (near & ~pre) | buffer_ahead<N>(p, pre, v, dv, a, b, acc);
+  }
   const int cnt = __popc(near);
   const int inc = warp_inclusive_scan(cnt);
   const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
@@ -469,8 +524,9 @@ __device__ __forceinline__ void split_min_pass(const SsspParams &p, const Split 
 // Split, second pass, over every vertex (S and s are the new ones): the far
 // vertices below the new S (distance in [old S, new S)) form the next
 // frontier. Called by every thread of a grid of T threads (T a multiple of 32).
-__device__ __forceinline__ void split_apply_pass(const SsspParams &p, const Split &q, int t, int T) {
-  NearAcc acc;
+// Out of line: it runs once per split, and inlined its registers weighed on
+// the queue kernel's round loop (more spills under the kernel's cap).
+__device__ __noinline__ void split_apply_pass(const SsspParams &p, const Split &q, int t, int T, NearAcc &acc) {
   auto in_bucket = [&](unsigned dv) { return dv >= q.S_old && dv < q.S; };
   const int base = t - (int)lane_id();  // warp-uniform loops: the appends need the whole warp
   const bool vec = (reinterpret_cast<uintptr_t>(p.dist) & 15u) == 0;
@@ -531,13 +587,18 @@ __device__ __forceinline__ unsigned bucket_top(unsigned d, unsigned w) {
 __device__ __forceinline__ void publish_frontier(const SsspParams &p) {
   WsHeader *h = p.hdr;
   const unsigned long long nn = ld_volatile(&h->nf_near);
-  if (nn > 0 && ld_volatile(&h->nf_elig) == 0 && p.sub_delta) h->nf_sub = bucket_top(ld_volatile(&h->nf_hmin), p.sub_delta);
+  const bool advance = nn > 0 && ld_volatile(&h->nf_elig) == 0 && p.sub_delta;
+  if (advance) h->nf_sub = bucket_top(ld_volatile(&h->nf_hmin), p.sub_delta);
   h->aux[0] = nn;
   h->nf_near = 0ull;
   h->nf_elig = 0ull;
   h->nf_hmin = kInf;
   h->cursor2 = 0ull;
-  h->cursor = 0ull;
+  // queue level: the unit buffer holds the next round's units buffered ahead
+  // (it was emptied after the children); only a sub-split advance leaves
+  // heavy frontier entries for the parent phase to buffer
+  if (p.prebuffer) h->nf_append = advance ? 1u : 0u;
+  else h->cursor = 0ull;
   h->aux[2] = 0ull;    // the grid-level child's unit cursor
   h->launches = 0ull;  // the round's children have all finished: their pool slots are free
 }
@@ -584,6 +645,7 @@ __global__ void __launch_bounds__(1024) sssp_init(SsspParams p) {
     h->nf_split_old = 0u;
     h->nf_dmin = kInf;
     h->nf_hmin = kInf;
+    h->nf_append = 1u;  // the source's units (if it is heavy) are buffered by round 0's parent phase
   }
 }
 
@@ -976,7 +1038,8 @@ __global__ void __launch_bounds__(256) sssp_split_min(SsspParams p, unsigned r) 
 __global__ void __launch_bounds__(256) sssp_split_apply(SsspParams p, unsigned r) {
   phase_sync(p);
   if (s_ph.done) return;  // (flat level) the split found no vertex at or above S
-  split_apply_pass(p, read_split(), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  NearAcc acc;
+  split_apply_pass(p, read_split(), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, acc);
   if (!last_block_done(&p.hdr->done_blocks2)) return;
   if (threadIdx.x == 0) {
     finish_split(p);
@@ -1012,6 +1075,7 @@ __device__ bool queue_barrier(const SsspParams &p, unsigned k, int kind) {
     if (atomicAdd(&p.hdr->done_blocks2, 1u) == k * gridDim.x - 1) {
       if (kind == kBarChildren) {
         p.hdr->aux[1] = ld_volatile(&p.hdr->cursor2);
+        p.hdr->cursor = 0ull;  // every unit of the round is done: the commit buffers the next round's
       } else if (kind == kBarRound) {
         publish_frontier(p);
       } else if (kind == kBarSplitMin) {
@@ -1056,13 +1120,16 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
   unsigned k = 0, r = 0;
   for (;;) {
     const int nf = (int)s_ph.nf;
-    if (nf == 0) {
+    if (nf == 0 && s_ph.units == 0) {
       // the split: the far pile's smallest live distance, then the new frontier from it
       if (!p.delta) break;  // no split: an empty frontier ends the run
       split_min_pass(p, read_split(), gtid, G);
       if (!queue_barrier(p, ++k, kBarSplitMin)) return;
       if (s_ph.done) break;  // no vertex at or above the split: every distance is final
-      split_apply_pass(p, read_split(), gtid, G);
+      NearAcc sacc;
+      split_apply_pass(p, read_split(), gtid, G, sacc);
+      relaxed += sacc.pre_edges;
+      buf += sacc.pre_items;
       if (!queue_barrier(p, ++k, kBarSplitApply)) return;
       continue;
     }
@@ -1111,7 +1178,9 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
       }
       relax_inline_warp(p, a, b, (unsigned)f.y, r, S, work && nu == 0, ws);
     }
-    if (!queue_barrier(p, ++k, kBarPlain)) return;
+    // the units buffered ahead by the commit are in place since the round's
+    // barrier; a barrier is needed only when this phase may have added some
+    if (s_ph.append && !queue_barrier(p, ++k, kBarPlain)) return;
     // the consolidated child's loop: every warp's first unit is its own (no
     // atomic while units are fewer than warps), the rest come from a shared cursor
     const int total = (int)min(s_ph.units, (unsigned long long)p.max_units);
@@ -1143,6 +1212,8 @@ __global__ void __maxnreg__(40) sssp_queue(SsspParams p) {
     for (int i0 = gtid - lane; i0 < nn; i0 += G)
       commit_vertex(p, i0 + lane < nn, i0 + lane < nn ? __ldcg(p.fnext + i0 + lane) : 0, q, acc);
     flush_near(p, acc);
+    relaxed += acc.pre_edges;
+    buf += acc.pre_items;
     ++r;
     if (!queue_barrier(p, ++k, kBarRound)) return;
   }
