@@ -700,10 +700,13 @@ static dpc_status tree_call(int op, const int32_t *coff, const int32_t *cidx, in
   int dev = 0;
   if ((st = current_device(&dev)) != DPC_OK) return st;
   if ((st = begin_call(workspace, stats, s)) != DPC_OK) return st;
-  const void *visit = level == DPC_QUEUE ? tree_queue_kernel(op) : tree_visit_kernel(level, op);
+  const void *visit = level == DPC_QUEUE ? tree_queue_kernel(op, tree_chained_postwork(n)) : tree_visit_kernel(level, op);
   resolve_device(dev, tuning, level, visit, visit, n, &c);
 
   TreeParams p;
+  p.chain = 0;  // the queue level sets its postwork form below
+  p.par = nullptr;
+  p.link = nullptr;
   std::memset(&p, 0, sizeof(p));
   p.coff = coff;
   p.cidx = cidx;
@@ -723,9 +726,17 @@ static dpc_status tree_call(int op, const int32_t *coff, const int32_t *cidx, in
     const size_t mu = tree_max_units(n, p.chunk);
     p.units = reinterpret_cast<int2 *>(static_cast<char *>(workspace) + kHeaderBytes);
     p.max_units = (int)(mu > (size_t)INT_MAX ? INT_MAX : mu);
-    if (level == DPC_QUEUE)
-      p.level_ends = reinterpret_cast<int *>(static_cast<char *>(workspace) + kHeaderBytes +
-                                             tree_units_bytes(n, level, p.chunk));
+    if (level == DPC_QUEUE) {
+      char *b = static_cast<char *>(workspace) + kHeaderBytes + tree_units_bytes(n, level, p.chunk);
+      p.level_ends = reinterpret_cast<int *>(b);
+      b += align_up(((size_t)n + 2) * sizeof(int), 256);
+      p.chain = tree_chained_postwork(n) ? 1 : 0;
+      if (p.chain) {
+        p.par = reinterpret_cast<int *>(b);
+        b += align_up((size_t)n * sizeof(int), 256);
+        p.link = reinterpret_cast<unsigned long long *>(b);
+      }
+    }
   }
   p.stats = stats;
   if (level == DPC_QUEUE) {

@@ -288,6 +288,9 @@ struct TreeParams {
   int2 *units;        // (node, chunk index): every level's buffers, carved from one cursor;
                       // the queue level stores int4 units (node, first child, end child, -) there
   int *level_ends;    // queue level: level L's units are [level_ends[L], level_ends[L+1])
+  int chain;          // queue level: chained postwork (trees below 2^24 nodes)
+  int *par;           // chained postwork: parent of each internal node (root: -1)
+  unsigned long long *link;  // chained postwork: pending reports (high 32 bits) and partial value (low)
   WsHeader *hdr;      // cursor: units handed out; queue level: done_blocks2 / round are its barrier
   dpc_stats *stats;
 };
@@ -298,8 +301,10 @@ cudaError_t tree_launch(TreeParams &p, dpc_level level, int root_blocks, cudaStr
 const void *tree_visit_kernel(dpc_level level, int op);
 // The queue level: every tree level, then every postwork level, in one cooperative grid.
 constexpr int kTreeQueueMaxThreads = 512;  // block size bound of the queue kernel (registers)
-const void *tree_queue_kernel(int op);
+const void *tree_queue_kernel(int op, bool chain);
 size_t tree_units_bytes(int n, dpc_level level, int chunk);
+// The queue level's postwork for trees of n nodes: chained (no level barriers) below 2^24 nodes.
+inline bool tree_chained_postwork(int n) { return n < (1 << 24); }
 cudaError_t tree_queue_launch(const TreeParams &p, int blocks, int threads, cudaStream_t s);
 
 }  // namespace dpc

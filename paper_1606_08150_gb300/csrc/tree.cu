@@ -336,12 +336,24 @@ __global__ void tree_init(TreeParams p) {
 // The grid level's recursion inside one cooperative grid: the levels top-down
 // (every child's leaf value, the internal children's units appended after the
 // level's own), each closed by a grid barrier whose last arriver records where
-// the next level's units end; then the postwork level by level bottom-up, a
-// barrier after each. No launch at all. A unit here is (node, first child, end
-// child): the range travels with the unit, so a level costs one dependent load
-// fewer than with (node, chunk index) units, and one pass both reserves (per
-// warp and batch of children) and writes. Values are combined exactly as at
-// the other levels.
+// the next level's units end; then the postwork. No launch at all. A unit here
+// is (node, first child, end child, first-unit flag): the range travels with
+// the unit, so a level costs one dependent load fewer than with (node, chunk
+// index) units, and one pass both reserves (per warp and batch of children)
+// and writes.
+//
+// The postwork runs without level barriers. A node's value is its children's
+// share: each child adds 1 (descendants) or makes it at least 1 (heights),
+// plus, from each internal child c, desc(c) or 1 + height(c). The first part
+// is known when the node's units are visited, so the visit adds it. The second
+// waits for the internal children, which are counted: pend[v] = 1 + the
+// internal children of v, par[c] = the parent of internal c. After the last
+// level, one pass takes the extra 1 from every internal node; whichever thread
+// brings pend[v] to 0 - that pass, or the last internal child reporting - knows
+// v's value is complete, adds it to the parent and reports there, up the
+// chain. Exactly one thread finishes each node, no thread waits, and a chain
+// is at most the tree's depth long. The values are sums and maxima of
+// integers, so the order of the additions does not matter.
 namespace {
 
 constexpr int kSmallUnits = 2;  // a child with more units has them written by its whole warp
@@ -383,13 +395,13 @@ __device__ bool tree_barrier(const TreeParams &p, unsigned k, int end_slot, int 
 // unit i of the root, whose units are never read back before the postwork
 __device__ __forceinline__ int4 root_unit(const TreeParams &p, int i, int ra, int rb) {
   const int a = ra + i * p.chunk;
-  return make_int4(p.root, a, a + min(p.chunk, rb - a), 0);
+  return make_int4(p.root, a, a + min(p.chunk, rb - a), i == 0 ? 1 : 0);
 }
 
 // unit q of a node whose children are [first, first + k)
 __device__ __forceinline__ int4 child_unit(const TreeParams &p, int c, int first, int k, int q) {
   const int a = first + q * p.chunk;
-  return make_int4(c, a, a + min(p.chunk, first + k - a), 0);
+  return make_int4(c, a, a + min(p.chunk, first + k - a), q == 0 ? 1 : 0);
 }
 
 }  // namespace
@@ -398,21 +410,24 @@ __device__ __forceinline__ int4 child_unit(const TreeParams &p, int c, int first
 // warps of the calling group (warp-uniform start `wstart`, stride `stride`, a
 // multiple of 32): every child's value set to a leaf's, the units of the
 // children with children appended after the level.
+template <bool CHAIN>
 __device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *units, int nroot, int lo, int hi,
                                                   int wstart, int stride, bool root_level, int ra, int rb,
                                                   unsigned long long &visited, unsigned long long &internal) {
   const int lane = lane_id();
   for (int i0 = lo + wstart; i0 < hi; i0 += stride) {  // warp-uniform
     const int i = i0 + lane;
-    int a = 0, b = 0;
+    int a = 0, b = 0, node = -1;
     if (i < hi) {
       const int4 u = root_level ? root_unit(p, i, ra, rb) : __ldcg(units + i);
       if (u.x >= 0) {
+        node = u.x;
         a = u.y;
         b = u.z;
       }
     }
     visited += b - a;
+    int inner = 0;  // internal children among this unit's
     int nb = ceil_div(b - a, kKidBatch);
     for (int d = kWarp / 2; d >= 1; d >>= 1) nb = max(nb, __shfl_xor_sync(0xffffffffu, nb, d));
     for (int j = 0; j < nb; ++j) {
@@ -449,7 +464,17 @@ __device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *uni
       for (int t = 0; t < kKidBatch; ++t) {
         if (c[t] >= 0) p.out[c[t]] = 0;
         const int nu = total && c[t] >= 0 ? units_for(p, kc[t]) : 0;
-        if (nu) internal++;
+        if (nu) {
+          internal++;
+          inner++;
+          if (CHAIN) {
+            // one pending report (its own token; its visit adds its internal
+            // children); a node with children is at least 1 high
+            p.link[c[t]] = 1ull << 32;
+            if (p.op != kDescendants) p.out[c[t]] = 1;
+            p.par[c[t]] = node;
+          }
+        }
         if (nu <= kSmallUnits)
           for (int q = 0; q < nu; ++q) units[pos + q] = child_unit(p, c[t], first[t], kc[t], q);
         // the units of larger children: the whole warp writes them, child by child
@@ -465,6 +490,28 @@ __device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *uni
         pos += nu;
       }
     }
+    // chained postwork: the node's share from its children known now (1 per
+    // child for descendants; the internal ones report the rest later) and its
+    // internal-children count, in one atomic on its link word; a node's units
+    // are consecutive, so runs of one node are combined over the warp first
+    // and one atomic per node and warp remains
+    if (!CHAIN) continue;
+    unsigned kids = (unsigned)(b - a), inn = (unsigned)inner;
+    const int prev = __shfl_up_sync(0xffffffffu, node, 1);
+    int start = lane == 0 || prev != node ? lane : 0;
+    for (int d = 1; d < kWarp; d <<= 1) start = max(start, __shfl_up_sync(0xffffffffu, start, d));
+    for (int d = 1; d < kWarp; d <<= 1) {
+      const unsigned ok = __shfl_up_sync(0xffffffffu, kids, d), oi = __shfl_up_sync(0xffffffffu, inn, d);
+      if (lane - d >= start) {
+        kids += ok;
+        inn += oi;
+      }
+    }
+    const int next = __shfl_down_sync(0xffffffffu, node, 1);
+    if (node >= 0 && (lane == kWarp - 1 || next != node)) {
+      const unsigned long long add = ((unsigned long long)inn << 32) + (p.op == kDescendants ? kids : 0u);
+      if (add) atomicAdd(p.link + node, add);
+    }
   }
 }
 
@@ -473,16 +520,17 @@ __device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *uni
 // stops at the first wide or empty level and publishes where (the depth and
 // that level's units) in the header for the other blocks. Kept out of line
 // so that its registers do not weigh on the wide levels' loop.
-__device__ __noinline__ void queue_narrow_stretch(const TreeParams &p, int nroot, int lo, int hi, int depth,
-                                                  unsigned long long *counts) {
+template <bool CHAIN>
+__device__ __forceinline__ void narrow_stretch_body(const TreeParams &p, int nroot, int lo, int hi, int depth,
+                                                    unsigned long long *counts) {
   __shared__ int s_hi;
   int4 *const units = reinterpret_cast<int4 *>(p.units);
   const int narrow = 2 * blockDim.x;
   const int ra = __ldg(p.coff + p.root), rb = __ldg(p.coff + p.root + 1);
   unsigned long long visited = 0, internal = 0;
   while (lo < hi && hi - lo <= narrow && depth < p.n) {
-    queue_visit_level(p, units, nroot, lo, hi, threadIdx.x - lane_id(), blockDim.x, depth == 0, ra, rb, visited,
-                      internal);
+    queue_visit_level<CHAIN>(p, units, nroot, lo, hi, threadIdx.x - lane_id(), blockDim.x, depth == 0, ra, rb,
+                             visited, internal);
     __syncthreads();  // the level's appends and the cursor are visible to the block
     if (threadIdx.x == 0) {
       s_hi = (int)min((unsigned long long)nroot + *reinterpret_cast<volatile unsigned long long *>(&p.hdr->cursor),
@@ -501,6 +549,18 @@ __device__ __noinline__ void queue_narrow_stretch(const TreeParams &p, int nroot
   }
   counts[0] += visited;
   counts[1] += internal;
+}
+
+// The stretch out of line, one function per postwork form (template
+// instances of an out-of-line function lost the kernel's register cap).
+__device__ __noinline__ void queue_narrow_stretch_chain(const TreeParams &p, int nroot, int lo, int hi, int depth,
+                                                        unsigned long long *counts) {
+  narrow_stretch_body<true>(p, nroot, lo, hi, depth, counts);
+}
+
+__device__ __noinline__ void queue_narrow_stretch_levels(const TreeParams &p, int nroot, int lo, int hi, int depth,
+                                                         unsigned long long *counts) {
+  narrow_stretch_body<false>(p, nroot, lo, hi, depth, counts);
 }
 
 // One postwork level: units [a0, a1) combine their children's values into
@@ -559,6 +619,56 @@ __device__ __forceinline__ void queue_post_level_block(const TreeParams &p, int 
   __syncthreads();  // the next narrow level reads these values
 }
 
+// The chained postwork (trees below 2^24 nodes, see the comment at the head
+// of the queue level). link[v] holds v's count of pending reports in its high
+// 32 bits (1 for v's own token plus its internal children) and, for
+// descendants, its partial value in the low 32 bits, so one atomic both
+// reports a child's share and returns everything reported before it: the
+// report that takes the count to 0 holds the node's final value. Heights keep
+// the value in the output (each report raises it with atomicMax, then takes
+// its count, fenced; the last one reads it after a fence): a compare-and-swap
+// on the packed word contended at nodes with hundreds of internal children.
+// Thread t of T takes units [t, t+T, ...) and removes the token at the first
+// unit of each internal node; whichever operation completes a node reports to
+// its parent, up the chain.
+constexpr unsigned long long kOneReport = 0xFFFFFFFF00000000ull;  // added: one count fewer
+
+template <int OP>
+__device__ __forceinline__ void queue_postwork_chain(const TreeParams &p, const int4 *units, int total, int t, int T) {
+  for (int i = t; i < total; i += T) {
+    const int4 u = __ldcg(units + i);
+    if (u.x < 0 || u.w == 0) continue;  // a unit after a node's first (or a placeholder)
+    int c = u.x;
+    unsigned long long old = atomicAdd(p.link + c, kOneReport);
+    if (old >> 32 != 1ull) continue;
+    unsigned val;
+    if (OP == kDescendants) {
+      val = (unsigned)old;
+    } else {
+      __threadfence();
+      val = (unsigned)__ldcg(p.out + c);
+    }
+    for (;;) {  // c is complete with value val
+      const int v = __ldcg(p.par + c);
+      if (OP == kDescendants) p.out[c] = (int)val;
+      if (v < 0) break;  // the root
+      if (OP == kDescendants) {
+        old = atomicAdd(p.link + v, (unsigned long long)val + kOneReport);
+        if (old >> 32 != 1ull) break;
+        val += (unsigned)old;
+      } else {
+        atomicMax(p.out + v, (int)(val + 1u));
+        __threadfence();
+        old = atomicAdd(p.link + v, kOneReport);
+        if (old >> 32 != 1ull) break;
+        __threadfence();
+        val = (unsigned)__ldcg(p.out + v);
+      }
+      c = v;
+    }
+  }
+}
+
 // 64 registers: four 256-thread blocks fit per SM, for wide trees whose
 // levels hold millions of units; deep narrow trees run fewer blocks (the host
 // sizes the grid), since their levels are short.
@@ -568,11 +678,11 @@ __device__ __forceinline__ void queue_post_level_block(const TreeParams &p, int 
 // a stretch of consecutive narrow levels alone, separated by block barriers,
 // while the other blocks wait at one grid barrier; it publishes where it
 // stopped (the depth, and the next level's units) before it arrives. The
-// postwork levels follow the same rule; there every block knows every level's
-// width from the recorded level boundaries, so all agree where a grid barrier
-// is needed: after a level that all blocks ran, and before one that follows
-// levels block 0 ran alone.
-template <int OP>
+// postwork of trees below 2^24 nodes is one pass with no barrier
+// (queue_postwork_chain); larger trees, whose wide levels make the visit's
+// extra atomics cost more than the barriers, run it level by level bottom-up,
+// a narrow level in block 0 alone as above.
+template <int OP, bool CHAIN>
 __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
   int4 *const units = reinterpret_cast<int4 *>(p.units);
   const int lane = lane_id();
@@ -582,13 +692,24 @@ __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
   const int ra = __ldg(p.coff + p.root), rb = __ldg(p.coff + p.root + 1);
   const int nroot = units_for(p, rb - ra);
   if (gtid == 0) {
-    p.out[p.root] = 0;
+    p.out[p.root] = !CHAIN || OP == kDescendants || rb == ra ? 0 : 1;
+    if (CHAIN) {
+      p.link[p.root] = 1ull << 32;
+      p.par[p.root] = -1;
+    }
     p.level_ends[0] = 0;
     p.level_ends[1] = nroot;
   }
   for (int q = gtid; q < nroot; q += G) units[q] = root_unit(p, q, ra, rb);
 
   unsigned k = 0;
+  // the root's value and counters before its units add to them: block 0 alone
+  // when the root level is narrow, else every block after a grid barrier
+  if (nroot > 2 * (int)blockDim.x) {
+    if (!tree_barrier(p, ++k, -1, 0)) return;
+  } else {
+    __syncthreads();
+  }
   int depth = 0;  // unit levels processed
   int lo = 0, hi = nroot;
   unsigned long long visited = 0, internal = 0;
@@ -596,7 +717,8 @@ __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
     if (hi - lo <= 2 * (int)blockDim.x) {
       if (blockIdx.x == 0) {
         unsigned long long counts[2] = {0, 0};
-        queue_narrow_stretch(p, nroot, lo, hi, depth, counts);
+        if (CHAIN) queue_narrow_stretch_chain(p, nroot, lo, hi, depth, counts);
+        else queue_narrow_stretch_levels(p, nroot, lo, hi, depth, counts);
         visited += counts[0];
         internal += counts[1];
       }
@@ -606,24 +728,28 @@ __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
       hi = (int)*reinterpret_cast<volatile unsigned long long *>(&p.hdr->aux[3]);
       continue;
     }
-    queue_visit_level(p, units, nroot, lo, hi, wbase, G, depth == 0, ra, rb, visited, internal);
+    queue_visit_level<CHAIN>(p, units, nroot, lo, hi, wbase, G, depth == 0, ra, rb, visited, internal);
     if (!tree_barrier(p, ++k, depth + 2, nroot)) return;
     lo = hi;
     hi = __ldcg(p.level_ends + depth + 2);
     ++depth;
   }
 
-  // postwork bottom-up
-  const int narrow = 2 * blockDim.x;
-  auto level_narrow = [&](int L) { return __ldcg(p.level_ends + L + 1) - __ldcg(p.level_ends + L) <= narrow; };
-  for (int L = depth - 1; L >= 0; --L) {
-    const int a0 = __ldcg(p.level_ends + L), a1 = __ldcg(p.level_ends + L + 1);
-    if (a1 - a0 <= narrow) {
-      if (blockIdx.x == 0) queue_post_level_block<OP>(p, a0, a1);
-      if (L > 0 && !level_narrow(L - 1) && !tree_barrier(p, ++k, -1, 0)) return;
-    } else {
-      queue_post_level<OP>(p, units, a0, a1, wbase, G);
-      if (!tree_barrier(p, ++k, -1, 0)) return;
+  if (CHAIN) {
+    // postwork: every level's units are [0, hi); every level's visit is done
+    queue_postwork_chain<OP>(p, units, hi, gtid, G);
+  } else {
+    const int narrow = 2 * blockDim.x;
+    auto level_narrow = [&](int L) { return __ldcg(p.level_ends + L + 1) - __ldcg(p.level_ends + L) <= narrow; };
+    for (int L = depth - 1; L >= 0; --L) {
+      const int a0 = __ldcg(p.level_ends + L), a1 = __ldcg(p.level_ends + L + 1);
+      if (a1 - a0 <= narrow) {
+        if (blockIdx.x == 0) queue_post_level_block<OP>(p, a0, a1);
+        if (L > 0 && !level_narrow(L - 1) && !tree_barrier(p, ++k, -1, 0)) return;
+      } else {
+        queue_post_level<OP>(p, units, a0, a1, wbase, G);
+        if (!tree_barrier(p, ++k, -1, 0)) return;
+      }
     }
   }
   if (p.stats) {
@@ -637,14 +763,15 @@ __global__ void __maxnreg__(64) tree_queue(TreeParams p) {
   }
 }
 
-const void *tree_queue_kernel(int op) {
-  return op == kDescendants ? (const void *)tree_queue<kDescendants> : (const void *)tree_queue<kHeight>;
+const void *tree_queue_kernel(int op, bool chain) {
+  if (chain) return op == kDescendants ? (const void *)tree_queue<kDescendants, true> : (const void *)tree_queue<kHeight, true>;
+  return op == kDescendants ? (const void *)tree_queue<kDescendants, false> : (const void *)tree_queue<kHeight, false>;
 }
 
 cudaError_t tree_queue_launch(const TreeParams &p, int blocks, int threads, cudaStream_t s) {
   TreeParams q = p;
   void *args[] = {&q};
-  return cudaLaunchCooperativeKernel(tree_queue_kernel(p.op), dim3(blocks), dim3(threads), args, 0, s);
+  return cudaLaunchCooperativeKernel(tree_queue_kernel(p.op, p.chain != 0), dim3(blocks), dim3(threads), args, 0, s);
 }
 
 // ------------------------------------------------------------------ host side
@@ -663,7 +790,11 @@ size_t tree_units_bytes(int n, dpc_level level, int chunk) {
 
 size_t tree_workspace_bytes(int n, dpc_level level, const LaunchCfg &c) {
   size_t b = kHeaderBytes + tree_units_bytes(n, level, c.chunk);
-  if (level == DPC_QUEUE) b += align_up(((size_t)n + 2) * sizeof(int), 256);  // where each level's units end
+  if (level == DPC_QUEUE) {
+    b += align_up(((size_t)n + 2) * sizeof(int), 256);  // where each level's units end
+    if (tree_chained_postwork(n))                       // parents and link words of internal nodes
+      b += align_up((size_t)n * sizeof(int), 256) + align_up((size_t)n * sizeof(unsigned long long), 256);
+  }
   return b;
 }
 
