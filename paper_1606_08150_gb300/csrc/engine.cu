@@ -95,7 +95,8 @@ struct Slot {
   int nf;             // SSSP: current frontier size
   unsigned long long next_count;  // SSSP: next frontier size; trees: units handed out
   int post_level;     // trees: level whose postwork runs
-  int pad[3];
+  int pre_edges;      // SSSP: EDGES tasks the commit emitted for the next round's heavy vertices
+  int pad[2];
 };
 
 struct Engine {
@@ -382,7 +383,9 @@ __device__ void transition(const Engine &e, int s, int nl) {
         sl.next_count = 0;
         sl.round += 1;
         sl.phase = P_RELAX;
-        sl.pending = ceil_div(nn, kRelaxItems);
+        // the commit already queued the heavy vertices' EDGES tasks: they are part of this phase
+        sl.pending = ceil_div(nn, kRelaxItems) + *reinterpret_cast<volatile int *>(&sl.pre_edges);
+        sl.pre_edges = 0;
       }
       __syncwarp();
       ntasks = emit_ranges(e, nl, T_RELAX, s, 0, nn, kRelaxItems, 0);
@@ -498,11 +501,13 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
         b = __ldg(job.off + f.x + 1);
         if (b - a > e.hdr->threshold) nu = ceil_div(b - a, e.hdr->chunk);
       }
-      // large vertices: one EDGES task per chunk into the next wave
-      const long long pos = reserve_tasks(e, nl, nu);
-      if (nu && pos >= 0)
-        for (int k = 0; k < nu; ++k) e.tasks[nl][pos + k] = make_task(T_EDGES, s, f.x, k, f.y);
-      extra = __reduce_add_sync(0xffffffffu, (unsigned)nu);
+      // large vertices: one EDGES task per chunk into the next wave - in round 0
+      // only (the source); from round 1 on the commit queued them already
+      const int emit = r == 0 ? nu : 0;
+      const long long pos = reserve_tasks(e, nl, emit);
+      if (emit && pos >= 0)
+        for (int k = 0; k < emit; ++k) e.tasks[nl][pos + k] = make_task(T_EDGES, s, f.x, k, f.y);
+      extra = __reduce_add_sync(0xffffffffu, (unsigned)emit);
       if (i < t.z && nu == 0) {
         sssp_relax_edges(e, s, v, a, b, (unsigned)f.y, r, 0, 1);
         work = b - a;
@@ -520,12 +525,29 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
       break;
     }
     case T_COMMIT: {
+      // the next frontier's (vertex, distance) entries; a heavy vertex's EDGES
+      // tasks go straight into the next wave, beside the next round's RELAX
+      // tasks, so a round takes two waves instead of three
       const SsspView v = sssp_view(e, s);
       const unsigned *dist = static_cast<const unsigned *>(job.out);
-      for (int i = t.y + lane; i < t.z; i += kWarp) {
-        const int vtx = __ldcg(v.fnext + i);
-        v.fcur[i] = make_int2(vtx, (int)__ldcg(dist + vtx));
+      int emitted = 0;
+      for (int i0 = t.y; i0 < t.z; i0 += kWarp) {  // warp-uniform
+        const int i = i0 + lane;
+        int nu = 0, vtx = 0;
+        unsigned d = 0;
+        if (i < t.z) {
+          vtx = __ldcg(v.fnext + i);
+          d = __ldcg(dist + vtx);
+          v.fcur[i] = make_int2(vtx, (int)d);
+          const int a = __ldg(job.off + vtx), b = __ldg(job.off + vtx + 1);
+          if (b - a > e.hdr->threshold) nu = ceil_div(b - a, e.hdr->chunk);
+        }
+        const long long pos = reserve_tasks(e, nl, nu);
+        if (nu && pos >= 0)
+          for (int k = 0; k < nu; ++k) e.tasks[nl][pos + k] = make_task(T_EDGES, s, vtx, k, (int)d);
+        emitted += (int)__reduce_add_sync(0xffffffffu, (unsigned)nu);
       }
+      if (lane == 0 && emitted) atomicAdd(&e.slots[s].pre_edges, emitted);
       break;
     }
     case T_VISIT: {
@@ -663,6 +685,7 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
     sl.nf = 0;
     sl.next_count = 0;
     sl.post_level = 0;
+    sl.pre_edges = 0;
     *reinterpret_cast<volatile int *>(e.slot_state + s) = 1;
     atomicAdd(&e.hdr->active, 1);
   }
