@@ -82,6 +82,7 @@ struct EngineHeader {
   unsigned long long snap_lo, snap_hi;
   int snap_exit;
   unsigned long long t_start;
+  unsigned long long mb_seen;  // the mailbox's taken count (read at the launch's first barrier)
   unsigned long long task_cap;   // capacity of one task list
   unsigned long long slot_bytes; // scratch bytes per slot
 };
@@ -730,11 +731,13 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
 // block to arrive snapshots the next wave's task count, the active count and
 // the status before it releases the others: they cannot change until every
 // block has read them (no block can reach the next release before all arrive).
-// The mailbox's posted count, read with acquire semantics at system scope (the
-// host's release store of the count orders its job descriptors before it).
-__device__ __forceinline__ unsigned long long mailbox_posted(const dpc_mailbox *mb) {
+// The mailbox's posted count. When it has moved past `seen`, the read is
+// followed by a system-scope fence (acquire: the host's release store of the
+// count orders its job descriptors before it); an unchanged count needs none,
+// which keeps the fence off the barriers of a busy engine with nothing new.
+__device__ __forceinline__ unsigned long long mailbox_posted(const dpc_mailbox *mb, unsigned long long seen) {
   const unsigned long long v = *reinterpret_cast<const volatile unsigned long long *>(&mb->posted);
-  __threadfence_system();
+  if (v != seen) __threadfence_system();
   return v;
 }
 
@@ -746,13 +749,17 @@ __device__ __forceinline__ unsigned long long mailbox_posted(const dpc_mailbox *
 __device__ void serve_decision(const Engine &e, unsigned long long next_tasks, int active, unsigned status) {
   EngineHeader &h = *e.hdr;
   const unsigned long long now = global_ns();
-  if (h.t_start == 0) h.t_start = now;
+  if (h.t_start == 0) {
+    h.t_start = now;
+    // the mailbox keeps its own count of admitted jobs; only this kernel
+    // writes it, so a copy read once per launch stays current
+    h.mb_seen = *reinterpret_cast<const volatile unsigned long long *>(&e.mb->taken);
+  }
   const unsigned long long age = now - h.t_start;
   const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / kWarp);
   const unsigned long long cap = DPC_MAILBOX_CAP < warps ? DPC_MAILBOX_CAP : warps;
-  // the mailbox keeps its own count of admitted jobs (only this kernel writes it)
-  unsigned long long lo = *reinterpret_cast<const volatile unsigned long long *>(&e.mb->taken);
-  unsigned long long posted = mailbox_posted(e.mb);
+  unsigned long long lo = h.mb_seen;
+  unsigned long long posted = mailbox_posted(e.mb, lo);
   int exit_now = status != 0u || age > 4 * e.limit_ns;
   if (!exit_now && next_tasks == 0 && active != 0) {
     // an admitted problem with no task queued can never finish (a bug or malformed input)
@@ -767,18 +774,35 @@ __device__ void serve_decision(const Engine &e, unsigned long long next_tasks, i
       const unsigned long long t0 = global_ns();
       while (posted == lo && global_ns() - t0 < kIdlePollNs) {
         __nanosleep(256);
-        posted = mailbox_posted(e.mb);
+        posted = mailbox_posted(e.mb, lo);
       }
     }
   }
   const unsigned long long hi = exit_now ? lo : (posted - lo > cap ? lo + cap : posted);
   h.snap_lo = lo;
   h.snap_hi = hi;
-  *reinterpret_cast<volatile unsigned long long *>(&e.mb->taken) = hi;
+  if (hi != lo) {
+    h.mb_seen = hi;
+    *reinterpret_cast<volatile unsigned long long *>(&e.mb->taken) = hi;
+  }
   h.snap_exit = exit_now;
 }
 
-__device__ bool grid_barrier(const Engine &e, int next_list) {
+// What every thread of a block needs after a barrier, read once per block by
+// its master thread (every thread reading the same header words after every
+// barrier put tens of thousands of requests on one L2 line per wave).
+struct WaveState {
+  unsigned long long n;     // tasks in the coming wave's list
+  unsigned long long next;  // snapshot: tasks queued for the wave after a finished one
+  int active;
+  unsigned status;
+  unsigned long long lo, hi;  // resident form: mailbox jobs the coming wave admits
+  int exit;                   // resident form: the kernel ends
+};
+__shared__ WaveState s_wave;
+
+// `wave_list`: the list the coming wave takes its tasks from.
+__device__ bool grid_barrier(const Engine &e, int next_list, int wave_list) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -807,6 +831,16 @@ __device__ bool grid_barrier(const Engine &e, int next_list) {
       }
     }
     __threadfence();
+    if (ok) {
+      const EngineHeader *h = e.hdr;
+      s_wave.n = *reinterpret_cast<const volatile unsigned long long *>(&h->count[wave_list]);
+      s_wave.next = *reinterpret_cast<const volatile unsigned long long *>(&h->snap_count);
+      s_wave.active = *reinterpret_cast<const volatile int *>(&h->snap_active);
+      s_wave.status = *reinterpret_cast<const volatile unsigned *>(&h->snap_status);
+      s_wave.lo = *reinterpret_cast<const volatile unsigned long long *>(&h->snap_lo);
+      s_wave.hi = *reinterpret_cast<const volatile unsigned long long *>(&h->snap_hi);
+      s_wave.exit = *reinterpret_cast<const volatile int *>(&h->snap_exit);
+    }
     s_ok = ok;
   }
   __syncthreads();
@@ -835,7 +869,7 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
     for (int i = gw; i < na; i += nw) admit(e, new_jobs[i], new_slots[i], l);
   }
   // (resident form: the barrier's last arriver also takes the first mailbox posts)
-  if (!grid_barrier(e, e.mb ? (int)(wave % 3) : -1)) return;
+  if (!grid_barrier(e, e.mb ? (int)(wave % 3) : -1, (int)(wave % 3))) return;
   unsigned long long relaxed = 0;
   for (int w = 0; w < max_waves; ++w, ++wave) {
     const int l = (int)(wave % 3), nl = (int)((wave + 1) % 3), ol = (int)((wave + 2) % 3);
@@ -846,8 +880,7 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
     }
     if (e.mb) {
       // resident form: the jobs posted before the barrier, one warp each, into the next wave's list
-      const unsigned long long lo = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->snap_lo);
-      const unsigned long long hi = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->snap_hi);
+      const unsigned long long lo = s_wave.lo, hi = s_wave.hi;
       if ((unsigned long long)gw < hi - lo) {
         const unsigned long long q = (lo + (unsigned long long)gw) % DPC_MAILBOX_CAP;
         dpc_job job;
@@ -858,7 +891,7 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
         admit(e, job, __ldcv(&e.mb->slots[q]), nl);
       }
     }
-    const unsigned long long n = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->count[l]);
+    const unsigned long long n = s_wave.n;
     // tasks are handed out kGrab at a time while many remain, one at a time near
     // the end of the wave: one shared cursor, far fewer atomics on it
     for (;;) {
@@ -892,13 +925,13 @@ __global__ void __launch_bounds__(256) engine_kernel(Engine e, const dpc_job *__
         tasks_done(e, cur, delta, nl);
       }
     }
-    if (!grid_barrier(e, nl)) return;
-    const unsigned long long nn = *reinterpret_cast<volatile unsigned long long *>(&e.hdr->snap_count);
-    const int active = *reinterpret_cast<volatile int *>(&e.hdr->snap_active);
-    const unsigned status = *reinterpret_cast<volatile unsigned *>(&e.hdr->snap_status);
+    if (!grid_barrier(e, nl, nl)) return;
+    const unsigned long long nn = s_wave.next;
+    const int active = s_wave.active;
+    const unsigned status = s_wave.status;
     if (e.mb) {
       // resident form: idle waves go on (the barrier polled the mailbox) until the exit decision
-      if (*reinterpret_cast<volatile int *>(&e.hdr->snap_exit)) {
+      if (s_wave.exit) {
         ++wave;
         break;
       }
