@@ -14,7 +14,8 @@
 //   EDGES   one chunk of edges of one vertex, 8 per lane
 //   COMMIT  freeze (vertex, distance) of up to 256 next-frontier vertices
 //   VISIT   up to 32 tree units (node, chunk of children), one per lane
-//   POST    postwork of up to 32 tree units
+//   POST    postwork of up to 32 tree units (every unit of the tree at once,
+//           in one wave: see the tree pieces below)
 // Tasks made while a wave runs go to the next wave's list; waves are separated
 // by a grid barrier (bounded spin, so a fault cannot hang the GPU). Each
 // problem counts its outstanding tasks; the warp that finishes the last task
@@ -115,6 +116,9 @@ struct Engine {
 // (the other blocks wait at that barrier meanwhile, far below its own limit).
 constexpr unsigned long long kIdlePollNs = 20000;
 
+// A report to a tree node's link word: one count fewer (high 32 bits).
+constexpr unsigned long long kOneReport = 0xFFFFFFFF00000000ull;
+
 // Finished: results complete, then the state the caller polls. The state may
 // live in host memory (resident form), hence the system-scope fence.
 __device__ __forceinline__ void report_done(const Engine &e, int s) {
@@ -136,6 +140,8 @@ struct SsspView {
 struct TreeView {
   int2 *units;
   int *levels;
+  int *par;                  // parent of each internal node (root: -1)
+  unsigned long long *link;  // pending reports (high 32 bits), descendants' partial value (low)
   int max_units;
 };
 
@@ -159,7 +165,12 @@ __device__ __forceinline__ TreeView tree_view(const Engine &e, int s) {
   const size_t mu = (n > 0 ? n - 1 : 0) / (size_t)e.hdr->tree_chunk + n + 1;
   TreeView v;
   v.units = reinterpret_cast<int2 *>(b);
-  v.levels = reinterpret_cast<int *>(b + align_up(mu * sizeof(int2), 256));
+  b += align_up(mu * sizeof(int2), 256);
+  v.levels = reinterpret_cast<int *>(b);
+  b += align_up((n + 2) * sizeof(int), 256);
+  v.par = reinterpret_cast<int *>(b);
+  b += align_up(n * sizeof(int), 256);
+  v.link = reinterpret_cast<unsigned long long *>(b);
   v.max_units = (int)mu;
   return v;
 }
@@ -412,31 +423,20 @@ __device__ void transition(const Engine &e, int s, int nl) {
         // VISIT ranges are absolute unit indices
         ntasks = emit_ranges(e, nl, T_VISIT, s, start, end - start, kTreeItems, L + 1);
       } else {
-        // deepest level reached: postwork of level L, then upwards
-        const int lo = v.levels[L], hi = v.levels[L + 1];
+        // deepest level reached: the postwork of every unit at once (chained, one wave)
+        const int hi = v.levels[L + 1];
         if (lane == 0) {
           sl.phase = P_POST;
-          sl.post_level = L;
-          sl.pending = ceil_div(hi - lo, kTreeItems);
+          sl.post_level = 0;
+          sl.pending = ceil_div(hi, kTreeItems);
         }
         __syncwarp();
-        ntasks = emit_ranges(e, nl, T_POST, s, lo, hi - lo, kTreeItems, L);
+        ntasks = emit_ranges(e, nl, T_POST, s, 0, hi, kTreeItems, 0);
         if (ntasks == 0) done = true;
       }
       if (lane == 0 && e.stats) atomicMax(&e.stats->rounds, (unsigned)L + 2u);
     } else if (sl.phase == P_POST) {
-      const int L = sl.post_level;
-      if (L == 0) {
-        done = true;
-      } else {
-        const int lo = v.levels[L - 1], hi = v.levels[L];
-        if (lane == 0) {
-          sl.post_level = L - 1;
-          sl.pending = ceil_div(hi - lo, kTreeItems);
-        }
-        __syncwarp();
-        ntasks = emit_ranges(e, nl, T_POST, s, lo, hi - lo, kTreeItems, L - 1);
-      }
+      done = true;  // every node has reported
     }
   }
   if (ntasks == 0 && !done && sl.phase != P_DONE && lane == 0) {
@@ -593,10 +593,21 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
         total = 0;
       }
       int pos = total ? (int)base + inc - mine : 0;
+      const bool desc = job.kind == DPC_JOB_TREE_DESCENDANTS;
+      int node = -1;
+      if (i < t.z) node = __ldcg(v.units + i).x;
+      unsigned inner = 0;
 #pragma unroll
       for (int j = 0; j < kEngTreeChunk; ++j) {
         if (c[j] >= 0) out[c[j]] = 0;
         const int nu = total && kc[j] > 0 ? ceil_div(kc[j], tc) : 0;
+        if (nu) {
+          // one pending report (its own token); a node with children is at least 1 high
+          inner++;
+          v.link[c[j]] = 1ull << 32;
+          if (!desc) out[c[j]] = 1;
+          v.par[c[j]] = node;
+        }
         if (nu <= 2)
           for (int q = 0; q < nu; ++q) v.units[pos + q] = make_int2(c[j], q);
         // a larger child's units are written by the whole warp
@@ -610,40 +621,70 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
         }
         pos += nu;
       }
+      // the node's share known now (1 per child for descendants; its internal
+      // children report the rest) and its internal-children count, one atomic
+      // per run of one node's units in the warp
+      unsigned kids = (unsigned)(b - a);
+      const int prev = __shfl_up_sync(0xffffffffu, node, 1);
+      int start = lane == 0 || prev != node ? lane : 0;
+      for (int d = 1; d < kWarp; d <<= 1) start = max(start, __shfl_up_sync(0xffffffffu, start, d));
+      for (int d = 1; d < kWarp; d <<= 1) {
+        const unsigned ok = __shfl_up_sync(0xffffffffu, kids, d), oi = __shfl_up_sync(0xffffffffu, inner, d);
+        if (lane - d >= start) {
+          kids += ok;
+          inner += oi;
+        }
+      }
+      const int next = __shfl_down_sync(0xffffffffu, node, 1);
+      if (node >= 0 && (lane == kWarp - 1 || next != node)) {
+        const unsigned long long add = ((unsigned long long)inner << 32) + (desc ? kids : 0u);
+        if (add) atomicAdd(v.link + node, add);
+      }
       work = b - a;
       break;
     }
     case T_POST: {
+      // lane per unit: at a node's first unit (chunk index 0) remove the
+      // node's own token; whichever report completes a node carries its value
+      // to the parent, up the chain (the tree queue level's chained postwork)
       const TreeView v = tree_view(e, s);
-      const int tc = e.hdr->tree_chunk;
       int *out = static_cast<int *>(job.out);
+      const bool desc = job.kind == DPC_JOB_TREE_DESCENDANTS;
       const int i = t.y + lane;
-      int node = -1, a = 0, b = 0;
+      int c = -1;
       if (i < t.z) {
         const int2 u = __ldcg(v.units + i);
-        if (u.x >= 0) {
-          node = u.x;
-          a = __ldg(job.off + u.x) + u.y * tc;
-          b = min(__ldg(job.off + u.x + 1), a + tc);
+        if (u.x >= 0 && u.y == 0) c = u.x;
+      }
+      if (c >= 0) {
+        unsigned long long old = atomicAdd(v.link + c, kOneReport);
+        if (old >> 32 == 1ull) {
+          unsigned val;
+          if (desc) {
+            val = (unsigned)old;
+          } else {
+            __threadfence();
+            val = (unsigned)__ldcg(out + c);
+          }
+          for (;;) {  // c is complete with value val
+            const int p = __ldcg(v.par + c);
+            if (desc) out[c] = (int)val;
+            if (p < 0) break;  // the root
+            if (desc) {
+              old = atomicAdd(v.link + p, (unsigned long long)val + kOneReport);
+              if (old >> 32 != 1ull) break;
+              val += (unsigned)old;
+            } else {
+              atomicMax(out + p, (int)(val + 1u));
+              __threadfence();
+              old = atomicAdd(v.link + p, kOneReport);
+              if (old >> 32 != 1ull) break;
+              __threadfence();
+              val = (unsigned)__ldcg(out + p);
+            }
+            c = p;
+          }
         }
-      }
-      int c[kEngTreeChunk], val[kEngTreeChunk];
-#pragma unroll
-      for (int j = 0; j < kEngTreeChunk; ++j)
-        c[j] = a + j < b ? checked_index(__ldg(job.col + a + j), job.n, &e.hdr->status) : -1;
-#pragma unroll
-      for (int j = 0; j < kEngTreeChunk; ++j) val[j] = c[j] >= 0 ? __ldcg(out + c[j]) : 0;
-      unsigned sum = 0;
-      int h = 0;
-#pragma unroll
-      for (int j = 0; j < kEngTreeChunk; ++j) {
-        if (c[j] < 0) continue;
-        sum += 1u + (unsigned)val[j];
-        h = max(h, 1 + val[j]);
-      }
-      if (node >= 0) {
-        if (job.kind == DPC_JOB_TREE_DESCENDANTS) atomicAdd(reinterpret_cast<unsigned *>(out) + node, sum);
-        else atomicMax(out + node, h);
       }
       break;
     }
@@ -705,7 +746,10 @@ __device__ void admit(const Engine &e, const dpc_job &job, int s, int l) {
     const int nu = k > 0 ? ceil_div(k, tc) : 0;
     for (int q = lane; q < nu; q += kWarp) v.units[q] = make_int2(job.source, q);
     if (lane == 0) {
-      static_cast<int *>(job.out)[job.source] = 0;
+      // the root: its own token, no parent, at least 1 high when it has children
+      static_cast<int *>(job.out)[job.source] = job.kind == DPC_JOB_TREE_HEIGHT && nu > 0 ? 1 : 0;
+      v.link[job.source] = 1ull << 32;
+      v.par[job.source] = -1;
       v.levels[0] = 0;
       v.levels[1] = nu;
       sl.next_count = (unsigned long long)nu;
@@ -994,7 +1038,8 @@ size_t slot_bytes_for(int max_n, int tree_chunk) {
   const size_t sssp = align_up(n * sizeof(int2), 256) + align_up(n * sizeof(int), 256) +
                       align_up(n * sizeof(unsigned), 256);
   const size_t mu = (n > 0 ? n - 1 : 0) / (size_t)tree_chunk + n + 1;
-  const size_t tree = align_up(mu * sizeof(int2), 256) + align_up((n + 2) * sizeof(int), 256);
+  const size_t tree = align_up(mu * sizeof(int2), 256) + align_up((n + 2) * sizeof(int), 256) +
+                      align_up(n * sizeof(int), 256) + align_up(n * sizeof(unsigned long long), 256);
   return align_up(sssp > tree ? sssp : tree, 256);
 }
 
