@@ -231,50 +231,6 @@ __device__ __forceinline__ int emit_ranges(const Engine &e, int l, int kind, int
 // together outgrow L2, so they stream with the evict-first hint: the slots'
 // distances and stamps, gathered at random every round, stay in L2.
 
-__device__ __forceinline__ void sssp_relax_edges(const Engine &e, int s, const SsspView &v, int a, int b,
-                                                 unsigned du, unsigned r, int t, int T) {
-  const int *__restrict__ col = e.slots[s].job.col;
-  const unsigned *__restrict__ w = e.slots[s].job.w;
-  unsigned *dist = static_cast<unsigned *>(e.slots[s].job.out);
-  for (int e0 = a + t; e0 < b; e0 += kEdgeBatch * T) {
-    int vv[kEdgeBatch];
-    unsigned d[kEdgeBatch];
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q) {
-      const int ed = e0 + q * T;
-      vv[q] = -1;
-      d[q] = kInfU;
-      if (ed < b) {
-        const unsigned long long nd = (unsigned long long)du + __ldcs(w + ed);
-        vv[q] = checked_index(__ldcs(col + ed), e.slots[s].job.n, &e.hdr->status);
-        if (nd >= kInfU) eng_fail(e, DPC_ERR_OVERFLOW);
-        else d[q] = (unsigned)nd;
-      }
-    }
-    unsigned cur[kEdgeBatch];
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q) cur[q] = (vv[q] >= 0 && d[q] != kInfU) ? __ldcg(dist + vv[q]) : 0u;
-    unsigned improved = 0;
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q)
-      if (d[q] < cur[q] && d[q] < atomicMin(dist + vv[q], d[q])) improved |= 1u << q;
-    unsigned fresh = 0;
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q)
-      if ((improved >> q & 1u) && atomicExch(v.stamp + vv[q], r) != r) fresh |= 1u << q;
-    const int cnt = __popc(fresh);
-    cg::coalesced_group g = cg::coalesced_threads();
-    const int excl = cg::exclusive_scan(g, cnt);
-    const int total = g.shfl(excl + cnt, g.size() - 1);
-    unsigned long long base = 0;
-    if (g.thread_rank() == 0 && total) base = atomicAdd(&e.slots[s].next_count, (unsigned long long)total);
-    base = g.shfl(base, 0) + excl;
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q)
-      if (fresh >> q & 1u) v.fnext[base++] = vv[q];
-  }
-}
-
 // Per-warp staging of an EDGES task's new frontier vertices in shared memory
 // (kEngStage entries of one slot): the slot's list counter is reserved once
 // per flush instead of once per batch, and the buffer is flushed before the
@@ -302,11 +258,44 @@ __device__ __forceinline__ void eng_flush(const Engine &e, int s, const EngStage
 }
 
 // The EDGES form of sssp_relax_edges: a full warp over [a, b), staged appends.
+// One batch of up to kEdgeBatch candidate edges per lane (vertex vv, new
+// distance d; vv < 0: none): the distance gathers, atomicMin where the
+// candidate is smaller, the round's stamp for a vertex that dropped, and the
+// warp's new frontier vertices staged in shared memory (flushed to the slot's
+// list when the stage would overflow; the caller flushes the rest).
+__device__ __forceinline__ void relax_stage_batch(const Engine &e, int s, const SsspView &v, const int (&vv)[kEdgeBatch],
+                                                  const unsigned (&d)[kEdgeBatch], unsigned r, const EngStage &st) {
+  unsigned *dist = static_cast<unsigned *>(e.slots[s].job.out);
+  unsigned cur[kEdgeBatch];
+#pragma unroll
+  for (int q = 0; q < kEdgeBatch; ++q) cur[q] = (vv[q] >= 0 && d[q] != kInfU) ? __ldcg(dist + vv[q]) : 0u;
+  unsigned improved = 0;
+#pragma unroll
+  for (int q = 0; q < kEdgeBatch; ++q)
+    if (d[q] < cur[q] && d[q] < atomicMin(dist + vv[q], d[q])) improved |= 1u << q;
+  unsigned fresh = 0;
+#pragma unroll
+  for (int q = 0; q < kEdgeBatch; ++q)
+    if ((improved >> q & 1u) && atomicExch(v.stamp + vv[q], r) != r) fresh |= 1u << q;
+  const int cnt = __popc(fresh);
+  const int inc = warp_inclusive_scan(cnt);
+  const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
+  if (total == 0) return;
+  if (*st.cnt + total > kEngStage) eng_flush(e, s, st);
+  int pos = *st.cnt + inc - cnt;
+#pragma unroll
+  for (int q = 0; q < kEdgeBatch; ++q)
+    if (fresh >> q & 1u) st.buf[pos++] = vv[q];
+  __syncwarp();
+  if (lane_id() == kWarp - 1) *st.cnt += total;
+  __syncwarp();
+}
+
+// The EDGES form: a full warp over [a, b) of one vertex, lane-strided.
 __device__ __forceinline__ void sssp_relax_edges_staged(const Engine &e, int s, const SsspView &v, int a, int b,
                                                         unsigned du, unsigned r, const EngStage &st) {
   const int *__restrict__ col = e.slots[s].job.col;
   const unsigned *__restrict__ w = e.slots[s].job.w;
-  unsigned *dist = static_cast<unsigned *>(e.slots[s].job.out);
   const int t = lane_id(), T = kWarp;
   for (int base0 = a; base0 < b; base0 += kEdgeBatch * T) {
     int vv[kEdgeBatch];
@@ -323,29 +312,48 @@ __device__ __forceinline__ void sssp_relax_edges_staged(const Engine &e, int s, 
         else d[q] = (unsigned)nd;
       }
     }
-    unsigned cur[kEdgeBatch];
+    relax_stage_batch(e, s, v, vv, d, r, st);
+  }
+}
+
+// The RELAX form: the lanes' own light vertices ([a, b), distance du; lanes
+// with `active` false have none) relaxed by the whole warp together - the
+// edges of the 32 vertices in one sequence, edge k of it taken by lane k mod
+// 32 (a search over the lanes' scanned degrees finds its vertex) - instead of
+// each lane walking its own vertex while the warp waits for the longest.
+__device__ __forceinline__ void sssp_relax_inline_warp(const Engine &e, int s, const SsspView &v, int a, int b,
+                                                       unsigned du, unsigned r, bool active, const EngStage &st) {
+  const int *__restrict__ col = e.slots[s].job.col;
+  const unsigned *__restrict__ w = e.slots[s].job.w;
+  const int lane = lane_id();
+  const int deg = active ? b - a : 0;
+  const int incl = warp_inclusive_scan(deg);
+  const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+  const int excl = incl - deg;
+  for (int base = 0; base < total; base += kWarp * kEdgeBatch) {  // warp-uniform
+    int vv[kEdgeBatch];
+    unsigned d[kEdgeBatch];
 #pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q) cur[q] = (vv[q] >= 0 && d[q] != kInfU) ? __ldcg(dist + vv[q]) : 0u;
-    unsigned improved = 0;
+    for (int q = 0; q < kEdgeBatch; ++q) {
+      const int k = base + q * kWarp + lane;
+      int owner = 0;
 #pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q)
-      if (d[q] < cur[q] && d[q] < atomicMin(dist + vv[q], d[q])) improved |= 1u << q;
-    unsigned fresh = 0;
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q)
-      if ((improved >> q & 1u) && atomicExch(v.stamp + vv[q], r) != r) fresh |= 1u << q;
-    const int cnt = __popc(fresh);
-    const int inc = warp_inclusive_scan(cnt);
-    const int total = __shfl_sync(0xffffffffu, inc, kWarp - 1);
-    if (total == 0) continue;
-    if (*st.cnt + total > kEngStage) eng_flush(e, s, st);
-    int pos = *st.cnt + inc - cnt;
-#pragma unroll
-    for (int q = 0; q < kEdgeBatch; ++q)
-      if (fresh >> q & 1u) st.buf[pos++] = vv[q];
-    __syncwarp();
-    if (t == kWarp - 1) *st.cnt += total;
-    __syncwarp();
+      for (int step = kWarp / 2; step >= 1; step >>= 1) {
+        const int m = owner + step;
+        if (__shfl_sync(0xffffffffu, excl, m & (kWarp - 1)) <= k && m < kWarp) owner = m;
+      }
+      const int ed = __shfl_sync(0xffffffffu, a, owner) + k - __shfl_sync(0xffffffffu, excl, owner);
+      const unsigned dl = __shfl_sync(0xffffffffu, du, owner);
+      vv[q] = -1;
+      d[q] = kInfU;
+      if (k < total) {
+        const unsigned long long nd = (unsigned long long)dl + __ldcs(w + ed);
+        vv[q] = checked_index(__ldcs(col + ed), e.slots[s].job.n, &e.hdr->status);
+        if (nd >= kInfU) eng_fail(e, DPC_ERR_OVERFLOW);
+        else d[q] = (unsigned)nd;
+      }
+    }
+    relax_stage_batch(e, s, v, vv, d, r, st);
   }
 }
 
@@ -509,10 +517,9 @@ __device__ int2 run_task(const Engine &e, int4 t, int nl, const EngStage &st) {
       if (emit && pos >= 0)
         for (int k = 0; k < emit; ++k) e.tasks[nl][pos + k] = make_task(T_EDGES, s, f.x, k, f.y);
       extra = __reduce_add_sync(0xffffffffu, (unsigned)emit);
-      if (i < t.z && nu == 0) {
-        sssp_relax_edges(e, s, v, a, b, (unsigned)f.y, r, 0, 1);
-        work = b - a;
-      }
+      const bool inl = i < t.z && nu == 0;
+      sssp_relax_inline_warp(e, s, v, a, b, (unsigned)f.y, r, inl, st);
+      if (inl) work = b - a;
       break;
     }
     case T_EDGES: {
