@@ -687,9 +687,10 @@ def bench_serve(count=4096, rate=2000.0, seed=5):
     base_cap = res["saturated"]["one_at_a_time"]["req_per_s"]
     for name, make in (("default", lambda: serve.Server(graphs, trees, waves_per_step=32)),
                        ("tuned", lambda: serve.server_from_cache(cache, graphs, trees)),
-                       ("resident", lambda: serve.ResidentServer(graphs, trees))):
+                       ("resident", lambda: serve.ResidentServer(graphs, trees)),
+                       ("resident_tuned", lambda: serve.server_from_cache(cache, graphs, trees, resident=True))):
         sweep, best = [], None
-        for r in (2000.0, 4000.0, 8000.0, 10000.0, 12000.0, 14000.0, 16000.0, 32000.0):
+        for r in (2000.0, 4000.0, 8000.0, 10000.0, 12000.0, 14000.0, 16000.0, 18000.0, 20000.0, 24000.0, 32000.0):
             reqs = serve.poisson_stream(np.random.default_rng(seed + 2), count, r, len(graphs), len(trees), sources)
             arr = np.array([q.arrival for q in reqs])
             srv = make()

@@ -314,13 +314,16 @@ class ResidentServer(Server):
 
 
 def server_from_cache(cache, graphs: Sequence[Resident], trees: Sequence[Resident], sssp_fraction: float = 0.6,
-                      **kw) -> "Server":
-    """A Server configured by the autotuner's entry for this request mix
+                      resident: bool = False, **kw) -> "Server":
+    """A Server (or, with resident=True, a ResidentServer, which has no steps)
+    configured by the autotuner's entry for this request mix
     (autotune.tune_engine, stored under autotune.mix_key); the engine's
     default configuration when the cache holds none."""
     from . import autotune
 
     p = cache.lookup(autotune.mix_key(graphs, trees, sssp_fraction)) or dict(autotune.ENGINE_DEFAULT)
+    if resident:
+        return ResidentServer(graphs, trees, tuning=autotune.engine_tuning(p), **kw)
     return Server(graphs, trees, waves_per_step=p["waves"], tuning=autotune.engine_tuning(p), **kw)
 
 

@@ -78,6 +78,18 @@ def test_tuned_engine_serves_the_mix_bit_exact(dpc):
         else:
             want = oracle.tree_height(trees_h[r.problem].coff, trees_h[r.problem].cidx, 0)
         assert np.array_equal(got[i], want), i
+    # the resident server from the same entry: the same results
+    rsrv = serve.server_from_cache(cache, graphs, trees, resident=True, slots=8, limit_us=2_000_000)
+    assert isinstance(rsrv, serve.ResidentServer)
+    got_r = {}
+
+    def keep_r(i, s):
+        n = graphs[reqs[i].problem].n if reqs[i].kind == dpc.JOB_SSSP else trees[reqs[i].problem].n
+        got_r[i] = rsrv.read_out(s, n)
+
+    assert rsrv.run(reqs, on_done=keep_r).status == 0
+    for i in range(len(reqs)):
+        assert np.array_equal(got_r[i], got[i]), i
 
 
 def test_engine_grid_size_from_tuning(dpc):
