@@ -196,3 +196,30 @@ def test_mailbox_host_side(lib):
     assert lib.dpc_mailbox_post(addr, None, 0) == dpc.ERR_INVALID_ARG
     assert lib.dpc_mailbox_post(addr, ctypes.byref(job), -1) == dpc.ERR_INVALID_ARG
     assert lib.dpc_mailbox_init(None) == dpc.ERR_INVALID_ARG
+
+
+def test_engine_serve_rejects_bad_arguments_on_the_host(lib):
+    """dpc_engine_serve checks its scalars and pointers before any CUDA call."""
+    from paper_1606_08150_gb300 import dpc
+
+    P = ctypes.c_void_p
+    lib.dpc_engine_serve.argtypes = [P, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P,
+                                     ctypes.c_uint32, P, P, P]
+    mb = dpc.MailboxLayout()
+    state = (ctypes.c_int32 * 4)()
+    ws = P(0x1000)
+    args = dict(ws=ws, bytes=1 << 30, slots=4, max_n=100, max_m=100, tun=None, mb=ctypes.addressof(mb), limit=1000,
+                state=ctypes.addressof(state))
+
+    def call(**kw):
+        a = dict(args, **kw)
+        return lib.dpc_engine_serve(a["ws"], a["bytes"], a["slots"], a["max_n"], a["max_m"], a["tun"], a["mb"],
+                                    a["limit"], a["state"], None, None)
+
+    assert call(slots=0) == dpc.ERR_INVALID_ARG
+    assert call(max_n=0) == dpc.ERR_INVALID_ARG
+    assert call(mb=None) == dpc.ERR_INVALID_ARG
+    assert call(state=None) == dpc.ERR_INVALID_ARG
+    assert call(limit=0) == dpc.ERR_INVALID_ARG
+    assert call(limit=10_000_001) == dpc.ERR_INVALID_ARG
+    assert call(ws=None) == dpc.ERR_WORKSPACE
