@@ -389,8 +389,9 @@ dpc_status dpc_engine_init(void *workspace, size_t workspace_bytes, int32_t slot
  * step can be captured in a CUDA graph and replayed after new admissions are
  * copied into the same arrays. The engine grid is every block that can be
  * resident (a cooperative launch), or tuning->parent_blocks when that is
- * smaller; tuning->threshold and tuning->chunk set the SSSP split of large
- * frontier vertices into EDGES tasks. Problems must fit the slot size (n <= max_n,
+ * smaller; tuning->threshold (default 32) and tuning->chunk (default 512
+ * edges) set the SSSP split of large frontier vertices into EDGES tasks.
+ * Problems must fit the slot size (n <= max_n,
  * m <= max_m). The engine checks every admitted descriptor on the device: one
  * that cannot be valid (unknown kind, a size beyond the slot, a missing array,
  * a source or root out of range, a slot out of range) is not run, its slot

@@ -167,12 +167,12 @@ def default_space(app: str, level: str) -> List[Dict[str, int]]:
 # split into EDGES tasks), the cooperative grid (parent_blocks, 0 = every
 # resident block) and the waves an engine step runs before it returns to the
 # request loop (waves). The default is the engine's own configuration.
-ENGINE_DEFAULT = {"threshold": 32, "chunk": 256, "parent_blocks": 0, "waves": 32}
+ENGINE_DEFAULT = {"threshold": 32, "chunk": 512, "parent_blocks": 0, "waves": 32}
 
 
 def engine_axes(sms: int) -> Dict[str, Sequence[int]]:
     """Values tried per knob (coordinate search around the default)."""
-    return {"threshold": (16, 32, 64), "chunk": (128, 256, 512), "parent_blocks": (0, 2 * sms, sms),
+    return {"threshold": (16, 32, 64), "chunk": (256, 512, 1024), "parent_blocks": (0, 2 * sms, sms),
             "waves": (16, 32, 64)}
 
 

@@ -11,7 +11,7 @@
 //   RELAX   up to 32 frontier vertices, one per lane; a vertex above the
 //           threshold is not relaxed inline but split into EDGES tasks: the
 //           consolidation buffer of the paper, at queue granularity
-//   EDGES   one chunk of edges of one vertex, 8 per lane
+//   EDGES   one chunk of edges of one vertex (512 by default, 16 per lane)
 //   COMMIT  freeze (vertex, distance) of up to 256 next-frontier vertices
 //   VISIT   up to 32 tree units (node, chunk of children), one per lane
 //   POST    postwork of up to 32 tree units (every unit of the tree at once,
@@ -1088,7 +1088,7 @@ dpc_status engine_cfg(const dpc_tuning *t, EngineCfg *c) {
   std::memset(&z, 0, sizeof(z));
   if (!t) t = &z;
   c->threshold = t->threshold > 0 ? t->threshold : (t->threshold < 0 ? 0 : 32);
-  c->chunk = t->chunk > 0 ? t->chunk : 256;
+  c->chunk = t->chunk > 0 ? t->chunk : 512;  // 512 edges per EDGES task: the autotuner's pick on the served mix
   c->tree_chunk = kEngTreeChunk;
   c->threads = 256;
   if (t->chunk < 0 || c->chunk > (1 << 24)) return DPC_ERR_INVALID_ARG;

@@ -44,6 +44,6 @@ def test_mix_key_and_engine_tuning():
     trees = [SimpleNamespace(n=1000), SimpleNamespace(n=1_000_000)]
     assert autotune.mix_key(graphs, trees, 0.6) == "engine/sssp60/graphs2^10-2^18/trees2^9-2^19"
     t = autotune.engine_tuning(dict(autotune.ENGINE_DEFAULT, parent_blocks=304))
-    assert (t.threshold, t.chunk, t.parent_blocks) == (32, 256, 304)
+    assert (t.threshold, t.chunk, t.parent_blocks) == (32, 512, 304)
     axes = autotune.engine_axes(152)
     assert all(autotune.ENGINE_DEFAULT[k] in v for k, v in axes.items())
