@@ -170,6 +170,18 @@ int32_t dpc_abi_version(void);
 dpc_status dpc_device_init(int device, size_t pending_launch_limit);
 
 /*
+ * Whether the current device can read and write memory at `p`: device or
+ * managed memory, or pinned host memory (cudaHostAlloc / cudaHostRegister)
+ * mapped into the device's address space at the same address, as it is
+ * under unified addressing. Writes 1 or 0 to *accessible (0 for a null
+ * pointer and for host memory the CUDA runtime does not know). Reads only
+ * the runtime's record of the allocation; nothing runs on the device.
+ * Returns DPC_ERR_INVALID_ARG for a null `accessible`, DPC_ERR_CUDA if the
+ * runtime cannot be queried.
+ */
+dpc_status dpc_memory_device_accessible(const void *p, int32_t *accessible);
+
+/*
  * Single-source shortest paths (Sec. III.A, Fig. 1b; Sec. V). CSR graph with
  * n vertices and m directed edges: off[n+1] (int32, off[0]=0, off[n]=m),
  * col[m] (int32 in [0,n)), w[m] (uint32 weights). dist[n] receives the
@@ -201,6 +213,12 @@ dpc_status dpc_sssp(const int32_t *off, const int32_t *col, const uint32_t *w, i
  * [0,ncols)), val[nnz] (float), x[ncols], y[nrows]. Rows with more than
  * tuning.threshold non-zeros go to a child kernel at the given level. Every
  * level sums each row in a fixed order, so results are bitwise reproducible.
+ * x, y and the workspace are device memory. The matrix arrays (off, col,
+ * val) may instead be pinned host memory that the device reads in place
+ * (dpc_memory_device_accessible says 1): the kernels then read col and val
+ * once per call over the host link, so a host-resident matrix needs no device
+ * copy (nor device memory); y is bitwise the same. The host link bounds that
+ * call, as it bounds copying the matrix over first.
  */
 dpc_status dpc_spmv_csr_workspace_size(int32_t nrows, int32_t nnz, dpc_level level, const dpc_tuning *tuning,
                                        size_t *bytes);

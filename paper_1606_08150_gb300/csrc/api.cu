@@ -225,6 +225,22 @@ dpc_status dpc_device_init(int device, size_t pending_launch_limit) {
   return init_locked(device, pending_launch_limit ? pending_launch_limit : kDefaultPendingLaunches);
 }
 
+dpc_status dpc_memory_device_accessible(const void *p, int32_t *accessible) {
+  if (!accessible) return DPC_ERR_INVALID_ARG;
+  *accessible = 0;
+  if (!p) return DPC_OK;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return DPC_ERR_CUDA;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+    *accessible = 1;
+  else if (a.type == cudaMemoryTypeHost)  // pinned: mapped at the same address under unified addressing
+    *accessible = a.devicePointer == p ? 1 : 0;
+  return DPC_OK;
+}
+
 // ------------------------------------------------------------------ SpMV
 
 dpc_status dpc_spmv_csr_workspace_size(int32_t nrows, int32_t nnz, dpc_level level, const dpc_tuning *tuning,

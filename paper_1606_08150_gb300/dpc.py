@@ -27,7 +27,7 @@ INF = 0xFFFFFFFF
 
 # entry points declared in include/dpc.h
 EXPORTS = (
-    "dpc_status_string", "dpc_abi_version", "dpc_device_init",
+    "dpc_status_string", "dpc_abi_version", "dpc_device_init", "dpc_memory_device_accessible",
     "dpc_sssp_workspace_size", "dpc_sssp",
     "dpc_spmv_csr_workspace_size", "dpc_spmv_csr", "dpc_spmv_csr_noalloc",
     "dpc_tree_workspace_size", "dpc_tree_descendants", "dpc_tree_height",
@@ -105,6 +105,8 @@ def _load_library() -> ctypes.CDLL:
     lib.dpc_abi_version.restype = i32
     lib.dpc_device_init.argtypes = [ctypes.c_int, sz]
     lib.dpc_device_init.restype = st
+    lib.dpc_memory_device_accessible.argtypes = [P, ctypes.POINTER(i32)]
+    lib.dpc_memory_device_accessible.restype = st
     lib.dpc_spmv_csr_workspace_size.argtypes = [i32, i32, st, P, P]
     lib.dpc_spmv_csr_workspace_size.restype = st
     lib.dpc_spmv_csr.argtypes = [P, P, P, i32, i32, i32, P, P, st, P, P, sz, P, P]
@@ -189,11 +191,23 @@ def _tuning(tuning: Optional[Tuning]):
     return ctypes.byref(tuning) if tuning is not None else None
 
 
-def _dptr(t: Optional[torch.Tensor], dtype: torch.dtype, name: str):
+def device_accessible(t: torch.Tensor) -> bool:
+    """dpc_memory_device_accessible: whether the current device can read the
+    tensor's memory in place (device memory, or pinned host memory mapped into
+    the device's address space)."""
+    if t.numel() == 0:
+        return True
+    flag = ctypes.c_int32(0)
+    _check(_lib.dpc_memory_device_accessible(t.data_ptr(), ctypes.byref(flag)), "dpc_memory_device_accessible")
+    return bool(flag.value)
+
+
+def _dptr(t: Optional[torch.Tensor], dtype: torch.dtype, name: str, host_ok: bool = False):
     if t is None:
         return None
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_cuda and not (host_ok and t.is_pinned() and device_accessible(t)):
+        raise ValueError(f"{name} must be a CUDA tensor" +
+                         (" or pinned host memory the device can read" if host_ok else ""))
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -233,15 +247,17 @@ def spmv_csr(off: torch.Tensor, col: torch.Tensor, val: torch.Tensor, x: torch.T
              level, tuning: Optional[Tuning] = None, workspace: Optional[torch.Tensor] = None,
              stats: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None,
              ncols: Optional[int] = None) -> int:
-    """y = A x (fp32) through dpc_spmv_csr; returns the status (raises on host-side errors)."""
+    """y = A x (fp32) through dpc_spmv_csr; returns the status (raises on host-side errors).
+    The matrix (off, col, val) may be pinned host memory the device reads in
+    place; x and y are CUDA tensors."""
     nrows = off.numel() - 1
     nnz = col.numel()
     ncols = x.numel() if ncols is None else ncols
     lvl = _level(level)
     if workspace is None:
-        workspace = _ws_tensor(spmv_csr_workspace_size(nrows, nnz, lvl, tuning), off.device)
-    st = _lib.dpc_spmv_csr(_dptr(off, torch.int32, "off"), _dptr(col, torch.int32, "col"),
-                           _dptr(val, torch.float32, "val"), nrows, ncols, nnz, _dptr(x, torch.float32, "x"),
+        workspace = _ws_tensor(spmv_csr_workspace_size(nrows, nnz, lvl, tuning), y.device)
+    st = _lib.dpc_spmv_csr(_dptr(off, torch.int32, "off", True), _dptr(col, torch.int32, "col", True),
+                           _dptr(val, torch.float32, "val", True), nrows, ncols, nnz, _dptr(x, torch.float32, "x"),
                            _dptr(y, torch.float32, "y"), lvl, _tuning(tuning), workspace.data_ptr(),
                            workspace.numel(), _dptr(stats, torch.uint8, "stats"), _stream(stream))
     if st not in (OK, ERR_DEVICE, ERR_OVERFLOW, ERR_DEPTH, ERR_TIMEOUT):

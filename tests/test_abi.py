@@ -129,6 +129,11 @@ def test_host_only_calls(lib):
         assert lib.dpc_pagerank_workspace_size(1000, 20000, level, None, ctypes.byref(out)) == 0
         assert out.value > 256 + 2 * 4000
     assert lib.dpc_pagerank_workspace_size(0, 0, 0, None, ctypes.byref(out)) == 1
+    # the accessibility query: a null pointer is simply not accessible; a null result is refused
+    flag = ctypes.c_int32(7)
+    lib.dpc_memory_device_accessible.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.dpc_memory_device_accessible(None, ctypes.byref(flag)) == 0 and flag.value == 0
+    assert lib.dpc_memory_device_accessible(fake, None) == 1
 
 
 def test_argument_errors_return_before_any_cuda_call(lib):
@@ -152,6 +157,23 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     assert pr(fake, fake, fake, 4, 4, 0.85, -1, fake, 4, None, fake, 1 << 20, None, None) == 1
     assert pr(fake, None, fake, 4, 4, 0.85, 3, fake, 4, None, fake, 1 << 20, None, None) == 1  # m > 0, no sources
     assert pr(fake, fake, fake, 4, 4, 0.85, 3, fake, 4, None, fake, 16, None, None) == 2  # workspace too small
+
+
+def test_binding_refuses_host_memory_the_device_cannot_read():
+    """SpMV's matrix arrays may be pinned host memory the device reads in
+    place; pageable host memory, and x or y on the host, are refused before
+    any call into the library."""
+    import torch
+
+    from paper_1606_08150_gb300 import dpc
+
+    off = torch.tensor([0, 1, 2], dtype=torch.int32)
+    col = torch.tensor([0, 1], dtype=torch.int32)
+    val = torch.ones(2, dtype=torch.float32)
+    x = torch.ones(2, dtype=torch.float32)
+    y = torch.empty(2, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        dpc.spmv_csr(off, col, val, x, y, "grid", workspace=torch.empty(1 << 16, dtype=torch.uint8))
 
 
 def test_bad_tuning_rejected(lib):

@@ -163,3 +163,25 @@ def test_full_size_zipf_1m(dpc, law):
         assert stats.status == 0
         if level != "flat":
             assert stats.buffered_items == int((np.diff(A.off) > 32).sum())
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_host_resident_matrix_read_in_place(dpc, level):
+    """The matrix in pinned host memory, read by the kernels in place over the
+    host link: y is bitwise the y of the same matrix in device memory; host
+    memory the device cannot read is refused before any launch."""
+    A = gen.zipf_csr(20000, 20000, s=1.5, lmax=20000, seed=11)
+    x = gen.vector(20000, 11)
+    h = [torch.from_numpy(a).pin_memory() for a in (A.off, A.col, A.val)]
+    assert all(dpc.device_accessible(t) for t in h)
+    y_dev, status, _ = run(dpc, A, x, level)
+    assert status == dpc.OK
+    xd = dev(x)
+    y = torch.full((A.nrows,), float("nan"), dtype=torch.float32, device="cuda")
+    assert dpc.spmv_csr(h[0], h[1], h[2], xd, y, level) == dpc.OK
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy().view(np.int32), y_dev.view(np.int32))
+    with pytest.raises(ValueError):
+        dpc.spmv_csr(torch.from_numpy(A.off), h[1], h[2], xd, y, level)  # pageable host memory
+    with pytest.raises(ValueError):
+        dpc.spmv_csr(h[0], h[1], h[2], torch.from_numpy(x).pin_memory(), y, level)  # x must be on the device
