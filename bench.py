@@ -611,17 +611,14 @@ def bench_kc_study(dpc, t):
     return {"workload": "tree descendants, 2,097,152-node heavy-tailed tree", "levels": study}
 
 
-def bench_serve(count=4096, rate=2000.0, seed=5):
-    """Batched + served stream: Poisson arrivals, 60% SSSP on R-MAT graphs of
-    2^10..2^18 vertices (edge factor 16, w in [1,100]), 40% tree descendants /
-    heights on heavy-tailed geometric trees of 10^3..10^6 nodes, sizes
-    log-uniform. Persistent engine with continuous batching vs one library call
-    per request (grid level), same stream, same GPU."""
+def serve_pool(seed=5):
+    """The served stream's problem pool: 24 R-MAT graphs of 2^10..2^18
+    vertices and 16 heavy-tailed trees of 10^3..10^6 nodes (log-uniform),
+    uploaded; returns graphs, their sources with out-edges, trees."""
     from paper_1606_08150_gb300 import gen, serve
 
     rng = np.random.default_rng(seed)
     graphs, sources, trees = [], [], []
-    t0 = time.time()
     for i in range(24):
         scale = int(rng.integers(10, 19))
         g = gen.rmat(scale, seed=1000 + i)
@@ -630,6 +627,33 @@ def bench_serve(count=4096, rate=2000.0, seed=5):
     for i in range(16):
         n = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
         trees.append(serve.upload_tree(gen.tree(n, seed=2000 + i)))
+    return graphs, sources, trees
+
+
+def profile_engine(count=256, seed=5):
+    """One saturated batch of the served mix through the stepped engine, every
+    step its own launch (no CUDA graph), so a profiler sees engine_kernel
+    launch by launch; prints the steps and the makespan."""
+    from paper_1606_08150_gb300 import serve
+
+    graphs, sources, trees = serve_pool(seed)
+    reqs = serve.poisson_stream(np.random.default_rng(seed + 2), count, 0.0, len(graphs), len(trees), sources)
+    srv = serve.Server(graphs, trees, slots=32, waves_per_step=32, use_graph=False)  # ~1 GB of slots
+    res = srv.run(reqs)
+    print(json.dumps({"profile_engine": {"requests": count, "steps": res.steps, "status": res.status,
+                                         "makespan_ms": round(res.makespan * 1e3, 3)}}))
+
+
+def bench_serve(count=4096, rate=2000.0, seed=5):
+    """Batched + served stream: Poisson arrivals, 60% SSSP on R-MAT graphs of
+    2^10..2^18 vertices (edge factor 16, w in [1,100]), 40% tree descendants /
+    heights on heavy-tailed geometric trees of 10^3..10^6 nodes, sizes
+    log-uniform. Persistent engine with continuous batching vs one library call
+    per request (grid level), same stream, same GPU."""
+    from paper_1606_08150_gb300 import serve
+
+    t0 = time.time()
+    graphs, sources, trees = serve_pool(seed)
     gen_s = time.time() - t0
     res = {"workload": f"{count} requests, Poisson {rate:g}/s, 60% SSSP (R-MAT 2^10..2^18), "
                        f"40% TD/TH (trees 1e3..1e6 nodes), pool of {len(graphs)} graphs + {len(trees)} trees",
@@ -1109,6 +1133,8 @@ def main():
                     help="with --profile-apps: R-MAT scale of the SSSP graph (w in [1,1000], source 0)")
     ap.add_argument("--profile-sssp-tuning", default=None,
                     help="with --profile-apps: near-far split and sub-split widths for SSSP, e.g. 200,8")
+    ap.add_argument("--profile-engine", action="store_true",
+                    help="one saturated batch of the served mix, stepped engine without a CUDA graph (for ncu)")
     ap.add_argument("--checked-overhead", action="store_true",
                     help="time a few calls with the regular and the bounds-checked library and print both")
     ap.add_argument("--timing-suite", action="store_true", help="internal: the calls --checked-overhead times")
@@ -1167,6 +1193,12 @@ def main():
         print(json.dumps({"checked_overhead": {k: {"regular_ms": runs["regular"][k], "checked_ms": runs["checked"][k],
                                                    "ratio": round(runs["checked"][k] / runs["regular"][k], 3)}
                                                for k in runs["regular"]}}))
+        return
+    if args.profile_engine:
+        from paper_1606_08150_gb300 import dpc as _dpc
+
+        _dpc.device_init(local, 0)
+        profile_engine()
         return
     if args.serve_only:
         from paper_1606_08150_gb300 import dpc as _dpc
