@@ -732,6 +732,7 @@ static dpc_status tree_call(int op, const int32_t *coff, const int32_t *cidx, in
   p.op = op;
   p.level = level;
   p.chunk = level == DPC_FLAT ? INT_MAX : c.chunk;
+  p.chunk_shift = level != DPC_FLAT && (c.chunk & (c.chunk - 1)) == 0 ? __builtin_ctz((unsigned)c.chunk) : -1;
   p.child_blocks = c.child_blocks;
   p.child_threads = c.child_threads;
   // every recursive grid keeps a postwork tail launch pending until its subtree

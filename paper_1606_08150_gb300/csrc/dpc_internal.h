@@ -281,6 +281,7 @@ struct TreeParams {
   int op;             // TreeOp
   int level;
   int chunk;          // children per unit
+  int chunk_shift;    // log2(chunk) when chunk is a power of two, else -1
   int child_blocks;   // KC_X grid for a recursive consolidated launch
   int child_threads;
   int max_units;

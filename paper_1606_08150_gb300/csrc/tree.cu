@@ -74,7 +74,11 @@ __device__ __forceinline__ void load_kids(const TreeParams &p, int k0, int b, in
 }
 
 __device__ __forceinline__ int units_for(const TreeParams &p, int k) {
-  return k > 0 ? (p.chunk == INT_MAX ? 1 : ceil_div(k, p.chunk)) : 0;
+  // a power-of-two chunk (the default 8) divides by a shift: on the narrow
+  // levels one warp's chain of dependent instructions is the level's cost
+  if (k <= 0) return 0;
+  if (p.chunk_shift >= 0) return ((k - 1) >> p.chunk_shift) + 1;
+  return p.chunk == INT_MAX ? 1 : ceil_div(k, p.chunk);
 }
 
 }  // namespace
@@ -498,6 +502,11 @@ __device__ __forceinline__ void queue_visit_level(const TreeParams &p, int4 *uni
     if (!CHAIN) continue;
     unsigned kids = (unsigned)(b - a), inn = (unsigned)inner;
     const int prev = __shfl_up_sync(0xffffffffu, node, 1);
+    if (!__any_sync(0xffffffffu, lane > 0 && node >= 0 && prev == node)) {  // no node holds two lanes
+      const unsigned long long add = ((unsigned long long)inn << 32) + (p.op == kDescendants ? kids : 0u);
+      if (node >= 0 && add) atomicAdd(p.link + node, add);
+      continue;
+    }
     int start = lane == 0 || prev != node ? lane : 0;
     for (int d = 1; d < kWarp; d <<= 1) start = max(start, __shfl_up_sync(0xffffffffu, start, d));
     for (int d = 1; d < kWarp; d <<= 1) {
