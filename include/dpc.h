@@ -308,7 +308,8 @@ dpc_status dpc_bfs_rec(const int32_t *off, const int32_t *col, int32_t n, int32_
                        size_t workspace_bytes, dpc_stats *stats, dpc_stream_t stream);
 
 /*
- * Graph colouring (Sec. V, the GC benchmark) by Jones-Plassmann rounds over an
+ * Graph colouring (Sec. V, the GC benchmark) by round sweep (the independent-set
+ * rounds of Jones-Plassmann, the colour being the round) over an
  * undirected graph given as a symmetric CSR, off[n+1] and col[m] (int32; both
  * directions of every edge present; self-loops ignored, duplicates allowed),
  * with the caller's vertex priorities priority[n] (uint32; the random draws of

@@ -251,7 +251,8 @@ class Coloring:
 
 
 def color_jp(off, col, prio, threshold: int = 32) -> Coloring:
-    """Jones-Plassmann colouring with the given priorities (ties: larger id wins)."""
+    """Round-sweep colouring: the independent-set rounds of Jones-Plassmann with
+    the given priorities (ties: larger id wins), the colour being the round."""
     off, col, prio = _c(off, np.int32), _c(col, np.int32), _c(prio, np.uint32)
     n = off.shape[0] - 1
     color = np.empty(n, np.int32)

@@ -34,7 +34,7 @@
  *   oracle_bfs                hop distance from a source by a FIFO queue
  *                             (Sec. V, BFS-Rec: the levels its recursion
  *                             settles on; unique, so any traversal order works)
- *   oracle_color_jp           graph colouring by Jones-Plassmann rounds (Sec. V,
+ *   oracle_color_jp           graph colouring by round sweep (Sec. V,
  *                             the GC benchmark): in round r every uncoloured
  *                             vertex whose priority beats all its uncoloured
  *                             neighbours takes colour r
@@ -625,8 +625,8 @@ static int outranks(const uint32_t *prio, int32_t u, int32_t v) {
 
 /*
  * Graph colouring, the GC benchmark of Sec. V (the paper names the benchmark;
- * the algorithm read here is Jones-Plassmann with the priorities given as
- * input). Symmetric CSR off[n+1], col[m] (self-loops ignored, duplicates
+ * the algorithm read here is the independent-set rounds of Jones-Plassmann
+ * with the priorities given as input, the colour being the round). Symmetric CSR off[n+1], col[m] (self-loops ignored, duplicates
  * harmless). Rounds r = 1, 2, ...: a vertex still uncoloured when round r
  * begins takes colour r unless a neighbour also uncoloured when the round began
  * outranks it. Writes color[n] (>= 1), and per round (arrays of capacity

@@ -1,6 +1,7 @@
 // Graph colouring (Sec. V, the GC benchmark) at the consolidation levels.
 //
-// Jones-Plassmann rounds with the caller's priorities: in round r every vertex
+// Round-sweep colouring (the independent-set rounds of Jones-Plassmann, the
+// colour being the round) with the caller's priorities: in round r every vertex
 // still uncoloured when the round began takes colour r unless a neighbour also
 // uncoloured at the round's start outranks it (higher priority, ties to the
 // larger id). The irregular loop is the neighbour scan of each uncoloured
